@@ -1,0 +1,184 @@
+/*
+ * jacobi.h — C ABI of the GB300 (sm_103a) temporally-blocked 3D 7-point Jacobi
+ * library (libjacobi_gb300.so).
+ *
+ * Method: Wittmann, Hager, Wellein, "Multicore-aware parallel temporal blocking
+ * of stencil codes for shared and distributed memory" (arXiv:0912.4506).
+ *   Eq. 1 (Sect. 1.1)   one cell update: B_ijk = 1/6 (A_i-1 + A_i+1 + A_j-1 +
+ *                       A_j+1 + A_k-1 + A_k+1);
+ *   Sect. 1.1           successive sweeps write grids A and B in turn;
+ *   Sect. 1.3           temporal blocking: several updates of a block while it
+ *                       is held on chip, each update shifted by one cell.
+ *
+ * Arithmetic: the six neighbours are summed left to right in the order of Eq. 1
+ * and the sum is multiplied by RN(1/6) of the compute precision (never divided),
+ * with no fused multiply-add.  FP64 grids compute in FP64, FP32 grids in FP32,
+ * bf16 grids load bf16, compute in FP32 and round to bf16 (nearest-even) after
+ * every sweep, also inside a temporally-blocked pass.  Results are therefore
+ * independent of the temporal-blocking depth and bit-identical to a plain
+ * sequential sweep loop.
+ *
+ * Grid layout (every grid argument): a padded array with a one-cell boundary
+ * layer.  Interior cells are 1..n per axis, boundary cells 0 and n+1.  Cell
+ * (i,j,k) is element  i + row_pitch * (j + (ny+2) * k);  x (i) is contiguous.
+ * row_pitch >= nx+2 and row_pitch * element_size must be a multiple of 16 bytes;
+ * every device pointer must be 16-byte aligned.  Elements i >= nx+2 of a row are
+ * padding: never read, never written.  The boundary layer holds fixed Dirichlet
+ * data and is never written by a sweep.
+ *
+ * Ownership: the caller owns every grid, every device buffer and the stream.
+ * The library owns only what a handle holds (plan, tensor-map descriptors and a
+ * small device status word), released by the matching destroy call.
+ *
+ * Errors: every call returns JAC_OK (0) or a negative JAC_E* code; nothing is
+ * thrown across the ABI.  Calls are asynchronous on the handle's stream: a
+ * device-side fault or timeout surfaces at jacobi_check() (or at the caller's
+ * next synchronisation).  Grids passed to one call must not alias.
+ */
+#ifndef JACOBI_GB300_H
+#define JACOBI_GB300_H
+
+#include <stddef.h>
+
+#if defined(__GNUC__)
+#define JAC_API __attribute__((visibility("default")))
+#else
+#define JAC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum jac_status {
+    JAC_OK = 0,
+    JAC_EINVAL = -1,       /* bad shape, pointer, alignment or argument            */
+    JAC_ENOMEM = -2,       /* device allocation for the handle failed              */
+    JAC_ECUDA = -3,        /* a CUDA runtime/driver call failed                    */
+    JAC_ETIMEOUT = -4,     /* a bounded device-side wait ran out (status word)     */
+    JAC_EUNSUPPORTED = -5  /* no kernel for this dtype/mode/config                 */
+};
+
+typedef enum { JAC_F64 = 0, JAC_F32 = 1, JAC_BF16 = 2 } jac_dtype;
+
+/* Kernel selection for jacobi_sweep_ex(). */
+typedef enum {
+    JAC_KERNEL_AUTO = 0,   /* planner: plain streaming or temporal blocking        */
+    JAC_KERNEL_PLAIN = 1,  /* one sweep per pass over HBM (Eq. 1, 2*elem B/LUP)   */
+    JAC_KERNEL_TB = 2      /* temporally blocked passes of depth t (Sect. 1.3)     */
+} jac_kernel;
+
+typedef struct jacobi_s *jacobi_t;
+
+/* Description of the launch sequence a sweep call will use (jacobi_plan). */
+typedef struct {
+    int kernel;            /* JAC_KERNEL_PLAIN or JAC_KERNEL_TB                    */
+    int t;                 /* depth of the full passes (1 for plain)              */
+    int passes;            /* number of kernel launches                           */
+    int remainder_t;       /* depth of the last pass (0 if all passes are full)   */
+    int tile_x, tile_y;    /* output tile of one CTA (cells)                      */
+    int ext_x, ext_y;      /* loaded tile including the t-cell halo              */
+    int kchunk;            /* output k-planes per CTA                             */
+    int threads;           /* threads per CTA                                     */
+    int smem_bytes;        /* dynamic shared memory per CTA                       */
+    int grid_x, grid_y, grid_z;
+} jacobi_plan_info;
+
+/*
+ * jacobi_create — bind two caller-owned device grids A and B (same dtype, shape,
+ * row_pitch) of an nx x ny x nz interior to a handle.
+ *   dtype      JAC_F64, JAC_F32 or JAC_BF16 (bf16: 16-bit bit patterns).
+ *   grid_a/b   device pointers, 16-byte aligned, (nz+2)*(ny+2)*row_pitch elements.
+ *   row_pitch  elements per row, >= nx+2, row_pitch*elem % 16 == 0.
+ *   stream     cudaStream_t to launch on (NULL: legacy default stream).
+ * Enqueues one copy of A's boundary layer into B, so only A needs the boundary
+ * data on entry.  nx, ny, nz >= 1.  Returns JAC_EINVAL for bad arguments.
+ */
+JAC_API int jacobi_create(jacobi_t *out, int nx, int ny, int nz, int dtype, void *grid_a,
+                  void *grid_b, long long row_pitch, void *stream);
+
+/*
+ * jacobi_sweep — nsweeps sweeps of Eq. 1, A -> B -> A ... (Sect. 1.1).
+ *   t          temporal-blocking depth request: 0 = planner's choice, 1 = plain
+ *              streaming kernel, t >= 2 = passes of depth min(t, deepest feasible)
+ *              with a shallower last pass when t does not divide nsweeps.
+ *   final_is_b set to 1 when the result is in B, else 0.  Every pass (one plain
+ *              sweep, or one blocked pass of several sweeps) reads one grid and
+ *              writes the other, so this is the parity of the number of passes.
+ * nsweeps == 0 is a no-op.  The result values are bit-identical for every t.
+ */
+JAC_API int jacobi_sweep(jacobi_t h, int nsweeps, int t, int *final_is_b);
+
+/* jacobi_sweep_ex — as jacobi_sweep, with the kernel family forced
+ * (JAC_KERNEL_TB with t == 1 runs the blocked kernel at depth 1). */
+JAC_API int jacobi_sweep_ex(jacobi_t h, int nsweeps, int t, int kernel, int *final_is_b);
+
+/* jacobi_plan — fill *info with the plan jacobi_sweep_ex(h, nsweeps, t, kernel)
+ * would execute, without launching anything. */
+JAC_API int jacobi_plan(jacobi_t h, int nsweeps, int t, int kernel, jacobi_plan_info *info);
+
+/*
+ * jacobi_sweep_rhs — nsweeps correction sweeps of the iterative refinement:
+ *   e' = (((((( e[i-1] + e[i+1]) + e[j-1]) + e[j+1]) + e[k-1]) + e[k+1]) + rho) * RN(1/6)
+ * on the handle's grids (A = e on entry, boundary layer zero), the Jacobi
+ * iteration of (I - J0) e = rho/6 with J0 the sweep of Eq. 1 on a zero
+ * boundary.  rho: device grid of the handle's dtype and layout (read only).
+ * dtype JAC_F32 or JAC_BF16 (JAC_EUNSUPPORTED otherwise).  t, final_is_b as in
+ * jacobi_sweep.
+ */
+JAC_API int jacobi_sweep_rhs(jacobi_t h, const void *rho, int nsweeps, int t,
+                     int *final_is_b);
+
+/*
+ * jacobi_residual_accumulate — the FP64 step of the iterative refinement, on an
+ * nx x ny x nz interior:
+ *   u_out = u_in + (double) e        on the interior;
+ *   rho   = s(u_out) - 6.0 * u_out   on the interior, s = the six-neighbour sum
+ *                                    of Eq. 1 in its order (boundary data of
+ *                                    u_in included), product rounded first;
+ * rho is stored in lo_dtype (JAC_F32 or JAC_BF16: RN to FP32, then nearest-even
+ * to bf16; JAC_F64 also accepted).  Only interior cells of u_out and rho are
+ * written: u_out's boundary layer must already hold the boundary data, rho's
+ * boundary layer is never read by the correction sweep.  u_in/u_out: distinct
+ * FP64 grids with row pitch u_pitch.  e/rho: lo_dtype grids with row pitch
+ * lo_pitch.  Asynchronous on `stream` (cudaStream_t, NULL = default stream).
+ */
+JAC_API int jacobi_residual_accumulate(int nx, int ny, int nz, const double *u_in,
+                               double *u_out, long long u_pitch, const void *e,
+                               void *rho, int lo_dtype, long long lo_pitch,
+                               void *stream);
+
+/*
+ * jacobi_adjoint — reverse sweeps for the gradient of L = sum(W * A_n) (A_n the
+ * result of n forward sweeps).  The handle's grids hold the adjoint field:
+ * A = lambda_n (W on the interior, zero boundary layer) on entry.  Each sweep
+ * applies the transpose of one forward sweep, which is the same stencil on a
+ * zero boundary, and adds RN(1/6) * lambda_s at the interior neighbour of every
+ * face cell of the boundary layer into grad_bdry (a grid of the handle's
+ * layout and dtype; only face cells are touched, in sweep order, one thread per
+ * cell: deterministic).  After nsweeps the interior of the final grid is dL/dA_0
+ * and grad_bdry (pre-set by the caller to W on the boundary layer) is dL/dg.
+ * dtype JAC_F32 or JAC_F64.
+ */
+JAC_API int jacobi_adjoint(jacobi_t h, void *grad_bdry, int nsweeps, int t,
+                   int *final_is_b);
+
+/* jacobi_check — wait for the handle's stream and report a device-side status
+ * (JAC_ETIMEOUT when a bounded wait ran out) or a CUDA error (JAC_ECUDA).  The
+ * status word is cleared. */
+JAC_API int jacobi_check(jacobi_t h);
+
+/* jacobi_destroy — release the handle (not the grids).  NULL is accepted. */
+JAC_API int jacobi_destroy(jacobi_t h);
+
+/* jacobi_strerror — static text for a status code. */
+JAC_API const char *jacobi_strerror(int code);
+
+/* jacobi_version — library version as 10000*major + 100*minor + patch. */
+JAC_API int jacobi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JACOBI_GB300_H */

@@ -1,0 +1,133 @@
+"""ctypes binding of libjacobi_gb300.so: the C ABI of include/jacobi.h, one
+Python function per C entry point with the same name.  Argument marshalling
+only; every step of the computation runs in the library's CUDA kernels.  There
+is no fallback: a missing library raises."""
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libjacobi_gb300.so")
+
+JAC_OK, JAC_EINVAL, JAC_ENOMEM, JAC_ECUDA, JAC_ETIMEOUT, JAC_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+JAC_F64, JAC_F32, JAC_BF16 = 0, 1, 2
+JAC_KERNEL_AUTO, JAC_KERNEL_PLAIN, JAC_KERNEL_TB = 0, 1, 2
+
+EXPORTS = ["jacobi_create", "jacobi_sweep", "jacobi_sweep_ex", "jacobi_plan",
+           "jacobi_sweep_rhs", "jacobi_residual_accumulate", "jacobi_adjoint",
+           "jacobi_check", "jacobi_destroy", "jacobi_strerror", "jacobi_version"]
+
+
+class JacobiError(RuntimeError):
+    def __init__(self, code, what=""):
+        self.code = code
+        msg = _strerror(code) if _lib is not None else str(code)
+        super().__init__(f"{what}: {msg} ({code})" if what else f"{msg} ({code})")
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int) for n in (
+        "kernel", "t", "passes", "remainder_t", "tile_x", "tile_y", "ext_x", "ext_y",
+        "kchunk", "threads", "smem_bytes", "grid_x", "grid_y", "grid_z")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+_lib = None
+
+
+def load(path=None):
+    """Load the library (no build step here: see paper_0912_4506_gb300.build)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library missing: {p} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(p)
+    P, I, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
+    PI = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "jacobi_create": ([ctypes.POINTER(P), I, I, I, I, P, P, LL, P], I),
+        "jacobi_sweep": ([P, I, I, PI], I),
+        "jacobi_sweep_ex": ([P, I, I, I, PI], I),
+        "jacobi_plan": ([P, I, I, I, ctypes.POINTER(PlanInfo)], I),
+        "jacobi_sweep_rhs": ([P, P, I, I, PI], I),
+        "jacobi_residual_accumulate": ([I, I, I, P, P, LL, P, P, I, LL, P], I),
+        "jacobi_adjoint": ([P, P, I, I, PI], I),
+        "jacobi_check": ([P], I),
+        "jacobi_destroy": ([P], I),
+        "jacobi_strerror": ([I], ctypes.c_char_p),
+        "jacobi_version": ([], I),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = res
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def _strerror(code):
+    return _lib.jacobi_strerror(code).decode()
+
+
+def _ck(rc, what):
+    if rc != JAC_OK:
+        raise JacobiError(rc, what)
+
+
+def jacobi_create(nx, ny, nz, dtype, grid_a, grid_b, row_pitch, stream):
+    h = ctypes.c_void_p()
+    _ck(load().jacobi_create(ctypes.byref(h), nx, ny, nz, dtype, grid_a, grid_b, row_pitch,
+                             stream), "jacobi_create")
+    return h
+
+
+def jacobi_sweep(h, nsweeps, t=0):
+    fb = ctypes.c_int(0)
+    _ck(load().jacobi_sweep(h, nsweeps, t, ctypes.byref(fb)), "jacobi_sweep")
+    return fb.value
+
+
+def jacobi_sweep_ex(h, nsweeps, t, kernel):
+    fb = ctypes.c_int(0)
+    _ck(load().jacobi_sweep_ex(h, nsweeps, t, kernel, ctypes.byref(fb)), "jacobi_sweep_ex")
+    return fb.value
+
+
+def jacobi_plan(h, nsweeps, t=0, kernel=JAC_KERNEL_AUTO):
+    info = PlanInfo()
+    _ck(load().jacobi_plan(h, nsweeps, t, kernel, ctypes.byref(info)), "jacobi_plan")
+    return info.as_dict()
+
+
+def jacobi_sweep_rhs(h, rho, nsweeps, t=0):
+    fb = ctypes.c_int(0)
+    _ck(load().jacobi_sweep_rhs(h, rho, nsweeps, t, ctypes.byref(fb)), "jacobi_sweep_rhs")
+    return fb.value
+
+
+def jacobi_residual_accumulate(nx, ny, nz, u_in, u_out, u_pitch, e, rho, lo_dtype, lo_pitch,
+                               stream):
+    _ck(load().jacobi_residual_accumulate(nx, ny, nz, u_in, u_out, u_pitch, e, rho, lo_dtype,
+                                          lo_pitch, stream), "jacobi_residual_accumulate")
+
+
+def jacobi_adjoint(h, grad_bdry, nsweeps, t=0):
+    fb = ctypes.c_int(0)
+    _ck(load().jacobi_adjoint(h, grad_bdry, nsweeps, t, ctypes.byref(fb)), "jacobi_adjoint")
+    return fb.value
+
+
+def jacobi_check(h):
+    _ck(load().jacobi_check(h), "jacobi_check")
+
+
+def jacobi_destroy(h):
+    _ck(load().jacobi_destroy(h), "jacobi_destroy")
+
+
+def jacobi_version():
+    return load().jacobi_version()

@@ -1,0 +1,209 @@
+"""PyTorch-facing API: device memory and streams from torch, every computation in
+libjacobi_gb300.so (through the ctypes binding in ``_lib``).
+
+A grid is a CUDA tensor of shape (nz+2, ny+2, nx+2) in the padded layout of
+include/jacobi.h (interior 1..n, one boundary layer, x contiguous).  Its rows may
+be padded: strides (row_pitch*(ny+2), row_pitch, 1) with row_pitch >= nx+2 and a
+row of row_pitch elements a multiple of 16 bytes.  ``alloc_grid`` returns such a
+view of a padded allocation.  bf16 grids are ``torch.bfloat16`` tensors.
+"""
+import torch
+
+from . import _lib
+from ._lib import (JAC_BF16, JAC_F32, JAC_F64, JAC_KERNEL_AUTO, JAC_KERNEL_PLAIN,
+                   JAC_KERNEL_TB, JacobiError)
+
+_DT = {torch.float64: JAC_F64, torch.float32: JAC_F32, torch.bfloat16: JAC_BF16}
+_NAME = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
+
+
+def torch_dtype(dtype):
+    return _NAME[dtype] if isinstance(dtype, str) else dtype
+
+
+def row_pitch(nx, dtype):
+    """Row pitch (elements) of the padded layout: nx+2 rounded up to 16 bytes."""
+    es = torch.empty((), dtype=torch_dtype(dtype)).element_size()
+    per = 16 // es
+    return -(-(nx + 2) // per) * per
+
+
+def alloc_grid(nx, ny, nz, dtype="f64", device="cuda", pitch=None):
+    """Zeroed grid (nz+2, ny+2, nx+2), a view of rows padded to ``pitch``."""
+    dt = torch_dtype(dtype)
+    px = row_pitch(nx, dt) if pitch is None else pitch
+    full = torch.zeros((nz + 2, ny + 2, px), dtype=dt, device=device)
+    return full[:, :, :nx + 2]
+
+
+def alloc_like(g):
+    """Zeroed grid with the shape, dtype, device and row pitch of ``g``."""
+    nx, ny, nz, px = grid_geom(g)
+    return alloc_grid(nx, ny, nz, g.dtype, g.device, pitch=px)
+
+
+def as_grid(full, nx):
+    """View an (nz+2, ny+2, row_pitch) tensor as the grid of an nx-wide interior."""
+    return full[:, :, :nx + 2]
+
+
+def _stream_ptr(device=None):
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def grid_geom(t):
+    """(nx, ny, nz, row_pitch) of a grid tensor; raises on a layout the library
+    cannot take."""
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("grids must be CUDA tensors")
+    if t.dim() != 3 or t.dtype not in _DT:
+        raise ValueError("grids are 3-D float64/float32/bfloat16 tensors")
+    nz2, ny2, nx2 = t.shape
+    px = t.stride(1)
+    if t.stride(2) != 1 or px < nx2 or t.stride(0) != px * ny2:
+        raise ValueError("grid must be (nz+2, ny+2, nx+2) with unit x stride and rows of "
+                         "row_pitch >= nx+2 elements")
+    if (px * t.element_size()) % 16 or t.data_ptr() % 16:
+        raise ValueError("rows must be a multiple of 16 bytes and the data 16-byte aligned")
+    return nx2 - 2, ny2 - 2, nz2 - 2, px
+
+
+class Jacobi:
+    """A pair of ping-pong grids bound to a library handle.
+
+    ``A`` holds the initial grid with its boundary layer; ``B`` (allocated with
+    A's layout if not given) receives A's boundary layer at construction.
+    """
+
+    def __init__(self, A, B=None):
+        nx, ny, nz, px = grid_geom(A)
+        self.nx, self.ny, self.nz, self.px = nx, ny, nz, px
+        self.A = A
+        self.B = alloc_like(A) if B is None else B
+        if grid_geom(self.B) != (nx, ny, nz, px) or self.B.dtype != A.dtype:
+            raise ValueError("B must match A (shape, dtype, row pitch)")
+        self.dtype = _DT[A.dtype]
+        self.device = A.device
+        with torch.cuda.device(self.device):
+            self._h = _lib.jacobi_create(nx, ny, nz, self.dtype, A.data_ptr(),
+                                         self.B.data_ptr(), px, _stream_ptr(self.device))
+
+    # ------------------------------------------------------------------
+    def sweep(self, nsweeps, t=0, kernel=JAC_KERNEL_AUTO):
+        """Run ``nsweeps`` sweeps; returns the tensor that holds the result."""
+        with torch.cuda.device(self.device):
+            fb = _lib.jacobi_sweep_ex(self._h, nsweeps, t, kernel)
+        return self.B if fb else self.A
+
+    def sweep_rhs(self, rho, nsweeps, t=0):
+        """Correction sweeps e' = (sum6(e) + rho) * RN(1/6) (A holds e, zero boundary)."""
+        if grid_geom(rho) != grid_geom(self.A) or rho.dtype != self.A.dtype:
+            raise ValueError("rho must match the grids (shape, dtype, row pitch)")
+        with torch.cuda.device(self.device):
+            fb = _lib.jacobi_sweep_rhs(self._h, rho.data_ptr(), nsweeps, t)
+        return self.B if fb else self.A
+
+    def adjoint(self, grad_bdry, nsweeps, t=0):
+        """Adjoint sweeps on A (= lambda_n, zero boundary); accumulates into grad_bdry."""
+        if grid_geom(grad_bdry) != grid_geom(self.A) or grad_bdry.dtype != self.A.dtype:
+            raise ValueError("grad_bdry must match the grids (shape, dtype, row pitch)")
+        with torch.cuda.device(self.device):
+            fb = _lib.jacobi_adjoint(self._h, grad_bdry.data_ptr(), nsweeps, t)
+        return self.B if fb else self.A
+
+    def plan(self, nsweeps, t=0, kernel=JAC_KERNEL_AUTO):
+        with torch.cuda.device(self.device):
+            return _lib.jacobi_plan(self._h, nsweeps, t, kernel)
+
+    def check(self):
+        with torch.cuda.device(self.device):
+            _lib.jacobi_check(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            with torch.cuda.device(self.device):
+                _lib.jacobi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sweep(A, nsweeps, t=0, kernel=JAC_KERNEL_AUTO):
+    """``nsweeps`` Jacobi sweeps of the grid ``A`` (not modified); returns a new
+    grid with the result."""
+    A2 = alloc_like(A)
+    A2.copy_(A)
+    j = Jacobi(A2)
+    out = j.sweep(nsweeps, t, kernel)
+    j.close()
+    return out
+
+
+def residual_accumulate(u_in, u_out, e, rho):
+    """FP64 refinement step: u_out = u_in + e (interior), rho = s(u_out) - 6 u_out
+    (only interior cells of u_out and rho are written)."""
+    nx, ny, nz, pu = grid_geom(u_in)
+    if grid_geom(u_out) != (nx, ny, nz, pu):
+        raise ValueError("u_out must match u_in")
+    gx, gy, gz, pl = grid_geom(e)
+    if (gx, gy, gz) != (nx, ny, nz) or grid_geom(rho) != (gx, gy, gz, pl) or rho.dtype != e.dtype:
+        raise ValueError("e and rho must match u's shape and each other")
+    if u_in.dtype != torch.float64 or u_out.dtype != torch.float64:
+        raise ValueError("u must be float64")
+    with torch.cuda.device(u_in.device):
+        _lib.jacobi_residual_accumulate(nx, ny, nz, u_in.data_ptr(), u_out.data_ptr(), pu,
+                                        e.data_ptr(), rho.data_ptr(), _DT[e.dtype], pl,
+                                        _stream_ptr(u_in.device))
+
+
+class Refiner:
+    """Mixed-precision iterative refinement of the Jacobi solve, with its buffers.
+
+    ``u0`` (float64 grid) holds the boundary data and the initial interior.  Each
+    outer step runs the FP64 residual (adding the previous correction), then
+    ``inner`` correction sweeps in ``dtype`` ("f32" or "bf16") from a zero
+    correction; after the last step the last correction is added.  In exact
+    arithmetic the result equals ``outer * inner`` plain sweeps of ``u0``.
+    """
+
+    def __init__(self, u0, dtype="f32"):
+        nx, ny, nz, _ = grid_geom(u0)
+        dt = torch_dtype(dtype)
+        self.u = [alloc_like(u0), alloc_like(u0)]
+        self.u[0].copy_(u0)
+        self.u[1].copy_(u0)
+        self.e0 = alloc_grid(nx, ny, nz, dt, u0.device)
+        self.e1 = alloc_like(self.e0)
+        self.rho = alloc_like(self.e0)
+        self.solver = Jacobi(self.e0, self.e1)
+
+    def run(self, outer, inner, t=0):
+        u, e0, rho = self.u, self.e0, self.rho
+        e_cur = e0
+        cur = 0
+        for _ in range(outer):
+            residual_accumulate(u[cur], u[1 - cur], e_cur, rho)
+            cur = 1 - cur
+            e0.zero_()
+            e_cur = self.solver.sweep_rhs(rho, inner, t)
+        residual_accumulate(u[cur], u[1 - cur], e_cur, rho)
+        return u[1 - cur]
+
+    def close(self):
+        self.solver.close()
+
+
+def refine_solve(u0, outer, inner, dtype="f32", t=0):
+    r = Refiner(u0, dtype)
+    out = r.run(outer, inner, t)
+    r.close()
+    return out
+
+
+__all__ = ["Jacobi", "Refiner", "sweep", "residual_accumulate", "refine_solve", "alloc_grid",
+           "alloc_like", "as_grid", "grid_geom", "row_pitch", "JacobiError",
+           "JAC_KERNEL_AUTO", "JAC_KERNEL_PLAIN", "JAC_KERNEL_TB"]

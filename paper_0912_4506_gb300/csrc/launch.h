@@ -1,0 +1,60 @@
+// Host-side registry of the compiled kernels, shared by the translation units of
+// the library (one per dtype/mode group, compiled in parallel) and the C ABI.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+namespace jac {
+
+struct TBArgs;
+
+using TBLaunchFn = cudaError_t (*)(const CUtensorMap& map, const TBArgs& a, dim3 grid,
+                                   cudaStream_t st);
+
+// One instantiation of the temporally-blocked kernel.
+struct TBEntry {
+    int dtype;      // 0 f64, 1 f32, 2 bf16
+    int mode;       // MODE_PLAIN, MODE_RHS, MODE_ADJ
+    int V;          // x cells per lane (extended tile width 32*V)
+    int NW;         // warps = rows of the extended tile
+    int T;          // temporal-blocking depth
+    int NS;         // TMA ring slots
+    size_t smem;    // dynamic shared memory bytes
+    TBLaunchFn launch;
+    const void* kernel;
+};
+
+using PlainLaunchFn = cudaError_t (*)(const void* A, void* B, const Geom& g, int kchunk,
+                                      dim3 grid, cudaStream_t st);
+
+struct PlainEntry {
+    int dtype;
+    int V;    // cells per lane
+    int WY;   // warps (rows) per CTA
+    PlainLaunchFn launch;
+    const void* kernel;
+};
+
+// Tables provided by the per-dtype translation units.
+const TBEntry* tb_entries_f64(int* n);
+const TBEntry* tb_entries_f32(int* n);
+const TBEntry* tb_entries_f32_rhs(int* n);
+const TBEntry* tb_entries_f32_adj(int* n);
+const TBEntry* tb_entries_bf16(int* n);
+const TBEntry* tb_entries_bf16_rhs(int* n);
+const PlainEntry* plain_entry_f64();
+const PlainEntry* plain_entry_f32();
+const PlainEntry* plain_entry_bf16();
+
+// Auxiliary kernels (aux.cu).
+cudaError_t launch_boundary_copy(int dtype, const void* A, void* B, const Geom& g,
+                                 cudaStream_t st);
+cudaError_t launch_residual(const double* u_in, double* u_out, const Geom& gu,
+                            const void* e, void* rho, int lo_dtype, const Geom& glo,
+                            cudaStream_t st);
+
+}  // namespace jac

@@ -1,0 +1,104 @@
+// Plain streaming sweep: one sweep of Eq. 1 per pass over HBM.
+//
+// Each thread owns V consecutive x cells of one row (one 16-byte vector for
+// V > 1, the interior-aligned cell for V == 1) and marches k through a chunk of
+// planes, keeping the k-1, k, k+1 values of its cells in registers (k-plane
+// register rotation), so each plane of A is read from HBM once and each plane
+// of B written once: 2 * sizeof(S) bytes per lattice-site update (Eq. 2 of the
+// paper's baseline model counts 16 B/LUP for FP64).  In-plane neighbours: x via
+// warp shuffles (global loads at the two warp edges), y via L1-cached loads of
+// the rows above and below, which the neighbouring warps stream anyway.
+#pragma once
+
+#include "common.cuh"
+
+namespace jac {
+
+template <class Tr, int V>
+__device__ __forceinline__ void load_vec(const typename Tr::S* __restrict__ p, bool ok,
+                                         typename Tr::C (&out)[V]) {
+    using S = typename Tr::S;
+    if (ok) {
+        const Vec<S, V> t = ldg_vec<S, V>(p);
+#pragma unroll
+        for (int e = 0; e < V; ++e) out[e] = Tr::ld(t.v[e]);
+    } else {
+#pragma unroll
+        for (int e = 0; e < V; ++e) out[e] = 0;
+    }
+}
+
+template <class Tr, int V, int WY>
+__global__ void __launch_bounds__(32 * WY)
+    plain_sweep_kernel(const typename Tr::S* __restrict__ A, typename Tr::S* __restrict__ B,
+                       const Geom g, const int kchunk) {
+    using S = typename Tr::S;
+    using C = typename Tr::C;
+    constexpr int XOFF = (V == 1) ? 1 : 0;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x;
+    const int x0 = XOFF + (int)(blockIdx.x * 32 + lane) * V;
+    const int y = 1 + (int)(blockIdx.y * WY + threadIdx.y);
+    if (y > g.ny) return;  // uniform over the warp
+    const int k0 = 1 + (int)blockIdx.z * kchunk;
+    if (k0 > g.nz) return;
+    const int k1 = min(g.nz, k0 + kchunk - 1);
+
+    // the lane's vector lies inside the row allocation (needed for shuffles even
+    // when none of its cells is interior)
+    const bool loadable = (x0 + V) <= g.px;
+    bool interior[V];
+    bool all_interior = true;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        interior[e] = loadable && (x0 + e >= 1) && (x0 + e <= g.nx);
+        all_interior = all_interior && interior[e];
+    }
+    const bool left_ok = (x0 >= 1);
+    const bool right_ok = (x0 + V) < g.px;
+
+    const long long row = g.lin(loadable ? x0 : 0, y, 0);
+    const C c6 = Tr::sixth();
+
+    C dn[V], ct[V], up[V], no[V], so[V];
+    load_vec<Tr, V>(A + row + g.plane * (k0 - 1), loadable, dn);
+    load_vec<Tr, V>(A + row + g.plane * k0, loadable, ct);
+
+    for (int k = k0; k <= k1; ++k) {
+        const long long base = row + g.plane * k;
+        load_vec<Tr, V>(A + base + g.plane, loadable, up);
+        load_vec<Tr, V>(A + base - g.px, loadable, no);
+        load_vec<Tr, V>(A + base + g.px, loadable, so);
+        C left = __shfl_up_sync(FULL, ct[V - 1], 1);
+        C right = __shfl_down_sync(FULL, ct[0], 1);
+        if (lane == 0) left = left_ok ? Tr::ld(__ldg(A + base - 1)) : C(0);
+        if (lane == 31) right = right_ok ? Tr::ld(__ldg(A + base + V)) : C(0);
+
+        Vec<S, V> outv;
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const C l = (e == 0) ? left : ct[e - 1];
+            const C r = (e == V - 1) ? right : ct[e + 1];
+            C s = Tr::add(l, r);
+            s = Tr::add(s, no[e]);
+            s = Tr::add(s, so[e]);
+            s = Tr::add(s, dn[e]);
+            s = Tr::add(s, up[e]);
+            outv.v[e] = Tr::st(Tr::mul(s, c6));
+        }
+        if (all_interior) {
+            *reinterpret_cast<Vec<S, V>*>(B + base) = outv;
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                if (interior[e]) B[base + e] = outv.v[e];
+        }
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            dn[e] = ct[e];
+            ct[e] = up[e];
+        }
+    }
+}
+
+}  // namespace jac

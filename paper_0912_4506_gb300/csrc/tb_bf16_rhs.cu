@@ -1,0 +1,14 @@
+// bf16-storage correction sweeps of the iterative refinement.
+#include "tb_inst.cuh"
+
+namespace jac {
+
+static const TBEntry kTB[] = {
+    JAC_TB(BF16, 2, 32, 1, MODE_RHS, 6), JAC_TB(BF16, 2, 32, 2, MODE_RHS, 6),
+    JAC_TB(BF16, 2, 32, 3, MODE_RHS, 6), JAC_TB(BF16, 2, 32, 4, MODE_RHS, 6),
+    JAC_TB(BF16, 2, 32, 5, MODE_RHS, 6), JAC_TB(BF16, 2, 32, 6, MODE_RHS, 6),
+    JAC_TB(BF16, 2, 32, 7, MODE_RHS, 6), JAC_TB(BF16, 2, 32, 8, MODE_RHS, 6),
+};
+JAC_TABLE(tb_entries_bf16_rhs, kTB)
+
+}  // namespace jac

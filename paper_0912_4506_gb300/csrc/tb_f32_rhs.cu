@@ -1,0 +1,14 @@
+// FP32 correction sweeps of the iterative refinement (temporally blocked).
+#include "tb_inst.cuh"
+
+namespace jac {
+
+static const TBEntry kTB[] = {
+    JAC_TB(F32, 2, 32, 1, MODE_RHS, 6), JAC_TB(F32, 2, 32, 2, MODE_RHS, 6),
+    JAC_TB(F32, 2, 32, 3, MODE_RHS, 6), JAC_TB(F32, 2, 32, 4, MODE_RHS, 6),
+    JAC_TB(F32, 2, 32, 5, MODE_RHS, 6), JAC_TB(F32, 2, 32, 6, MODE_RHS, 6),
+    JAC_TB(F32, 2, 32, 7, MODE_RHS, 6), JAC_TB(F32, 2, 32, 8, MODE_RHS, 6),
+};
+JAC_TABLE(tb_entries_f32_rhs, kTB)
+
+}  // namespace jac

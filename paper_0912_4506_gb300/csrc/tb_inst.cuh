@@ -1,0 +1,41 @@
+// Instantiation helpers for the per-dtype translation units.
+#pragma once
+
+#include "launch.h"
+#include "plain.cuh"
+#include "tb.cuh"
+
+namespace jac {
+
+template <class TR, int V, int NW, int T, int MODE, int NS>
+cudaError_t tb_launch(const CUtensorMap& map, const TBArgs& a, dim3 grid, cudaStream_t st) {
+    constexpr size_t smem = TBLayout<V, NW, T, NS, typename TR::S>::bytes();
+    tb_sweep_kernel<TR, V, NW, T, MODE, NS><<<grid, NW * 32, smem, st>>>(map, a);
+    return cudaGetLastError();
+}
+
+template <class TR, int V, int WY>
+cudaError_t plain_launch(const void* A, void* B, const Geom& g, int kchunk, dim3 grid,
+                         cudaStream_t st) {
+    using S = typename TR::S;
+    plain_sweep_kernel<TR, V, WY><<<grid, dim3(32, WY), 0, st>>>(
+        static_cast<const S*>(A), static_cast<S*>(B), g, kchunk);
+    return cudaGetLastError();
+}
+
+}  // namespace jac
+
+#define JAC_TB(TR, V, NW, T, MODE, NS)                                                    \
+    {TR::kDtype, MODE, V, NW, T, NS, ::jac::TBLayout<V, NW, T, NS, TR::S>::bytes(),       \
+     &::jac::tb_launch<TR, V, NW, T, MODE, NS>,                                          \
+     reinterpret_cast<const void*>(&::jac::tb_sweep_kernel<TR, V, NW, T, MODE, NS>)}
+
+#define JAC_PLAIN(TR, V, WY) \
+    {TR::kDtype, V, WY, &::jac::plain_launch<TR, V, WY>, \
+     reinterpret_cast<const void*>(&::jac::plain_sweep_kernel<TR, V, WY>)}
+
+#define JAC_TABLE(NAME, ARR)                                  \
+    const TBEntry* NAME(int* n) {                             \
+        *n = (int)(sizeof(ARR) / sizeof(ARR[0]));             \
+        return ARR;                                           \
+    }

@@ -1,0 +1,137 @@
+"""GPU parity of the plain and temporally-blocked sweeps against the CPU oracle,
+element by element and bit for bit (Eq. 1 with a fixed operand order and no FMA)."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from tests.helpers import first_diff, make_grid, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+PLAIN, TB = 1, 2
+
+
+def run_gpu(a, n, t, kernel, dtype, nx):
+    """Run on the GPU; returns the result grid without the row padding."""
+    from paper_0912_4506_gb300 import api
+    A = api.as_grid(to_dev(a, dtype), nx)
+    j = api.Jacobi(A)
+    out = j.sweep(n, t, kernel)
+    j.check()
+    res = to_host(out, dtype)
+    j.close()
+    return res
+
+
+def oracle_sweeps(a, n, nx, dtype, **kw):
+    return oracle.sweeps(a, n, nx=nx, dtype=dtype, **kw)[:, :, :nx + 2]
+
+
+SHAPES = [(64, 64, 64), (37, 29, 23), (1, 1, 1), (5, 3, 70), (130, 47, 9), (2, 33, 2)]
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_plain_kernel_bit_exact(shape, dtype):
+    nx, ny, nz = shape
+    a = make_grid(nx, ny, nz, dtype)
+    for n in (0, 1, 2, 5):
+        got = run_gpu(a, n, 1, PLAIN, dtype, nx)
+        want = oracle_sweeps(a, n, nx, dtype)
+        assert first_diff(got, want) is None, (n, first_diff(got, want))
+
+
+TMAX = {"f64": 4, "f32": 8, "bf16": 8}
+
+
+@pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_tb_kernel_bit_exact_every_depth(shape, dtype):
+    nx, ny, nz = shape
+    a = make_grid(nx, ny, nz, dtype)
+    n = 13  # not a multiple of most depths: remainder passes
+    want = oracle_sweeps(a, n, nx, dtype)
+    for t in range(1, TMAX[dtype] + 1):
+        got = run_gpu(a, n, t, TB, dtype, nx)
+        assert first_diff(got, want) is None, (t, first_diff(got, want))
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_tb_small_sweep_counts(dtype):
+    nx, ny, nz = 45, 38, 17
+    a = make_grid(nx, ny, nz, dtype)
+    for n in (0, 1, 2, 3, 7, 8, 9, 16, 17):
+        want = oracle_sweeps(a, n, nx, dtype)
+        for t in (2, 4, TMAX[dtype]):
+            got = run_gpu(a, n, t, TB, dtype, nx)
+            assert first_diff(got, want) is None, (n, t, first_diff(got, want))
+
+
+def test_config_64cubed_fp64_100_sweeps():
+    """64^3 FP64, 100 sweeps A->B->A, seeds 0/1: plain and every depth."""
+    a = make_grid(64, 64, 64, "f64")
+    want = oracle_sweeps(a, 100, 64, "f64")
+    assert first_diff(run_gpu(a, 100, 1, PLAIN, "f64", 64), want) is None
+    for t in (1, 2, 3, 4, 8, 16):
+        assert first_diff(run_gpu(a, 100, t, TB, "f64", 64), want) is None, t
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_row_padding_untouched(dtype):
+    """Elements beyond nx+2 in a row are never read nor written (NaN there would
+    poison any cell that read it)."""
+    from paper_0912_4506_gb300 import api
+    nx, ny, nz = 11, 9, 8
+    px = {"f64": 16, "f32": 20, "bf16": 24}[dtype]
+    a = make_grid(nx, ny, nz, dtype, px=px)
+    if dtype == "bf16":
+        a[:, :, nx + 2:] = 0x7FC0  # a NaN bit pattern
+    else:
+        a[:, :, nx + 2:] = np.nan
+    want = oracle_sweeps(a, 6, nx, dtype)
+    for t, kern in ((1, PLAIN), (3, TB), (6 if dtype != "f64" else 4, TB)):
+        Af = to_dev(a, dtype)
+        Bf = Af.clone()
+        j = api.Jacobi(api.as_grid(Af, nx), api.as_grid(Bf, nx))
+        out = to_host(j.sweep(6, t, kern), dtype)
+        j.check()
+        j.close()
+        assert np.array_equal(out, want), t
+        for g in (Af, Bf):
+            pad = to_host(g, dtype)[:, :, nx + 2:]
+            assert np.array_equal(pad.view(np.uint8), a[:, :, nx + 2:].view(np.uint8)), t
+
+
+def test_final_buffer_parity_reported():
+    from paper_0912_4506_gb300 import api
+    a = make_grid(20, 20, 20, "f64")
+    A = api.as_grid(to_dev(a, "f64"), 20)
+    j = api.Jacobi(A)
+    assert j.sweep(3, 1, PLAIN) is j.B        # 3 passes
+    assert j.sweep(4, 4, TB) is j.B           # 1 pass
+    assert j.sweep(8, 4, TB) is j.A           # 2 passes
+    assert j.sweep(0, 4, TB) is j.A
+    j.close()
+
+
+_FULL = {}
+
+
+def _oracle_512():
+    if "a" not in _FULL:
+        a = make_grid(512, 512, 512, "f64")
+        _FULL["a"] = a
+        _FULL["want"] = oracle_sweeps(a, 100, 512, "f64", nthreads=os.cpu_count() or 1)
+    return _FULL["a"], _FULL["want"]
+
+
+@pytest.mark.parametrize("t,kernel", [(1, PLAIN), (1, TB), (2, TB), (4, TB), (8, TB),
+                                      (16, TB)])
+def test_full_size_512cubed_fp64(t, kernel):
+    """512^3 FP64, 100 sweeps, the benchmark's launch configuration: every output
+    cell compared with the (OpenMP, bit-identical) oracle."""
+    a, want = _oracle_512()
+    got = run_gpu(a, 100, t, kernel, "f64", 512)
+    assert first_diff(got, want) is None, (t, first_diff(got, want))

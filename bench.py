@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 Jacobi library: GLUP/s and fraction of the roofline on
+the 512^3 FP64 7-point Jacobi workload (100 sweeps A->B->A, seeded U[0,1)
+interior and boundary), one JSON line on rank 0.
+
+A step is one call of the hot path: 100 sweeps of the 512^3 FP64 grid (the
+planner picks the kernel and the temporal-blocking depth unless --t is given).
+Inputs (1.09 GB per grid) are resident in HBM and far larger than L2 (129 MB),
+so no L2 flush is needed between steps.  Each step continues the iteration from
+the previous step's result; the work per step is identical.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 (torchrun, one rank per GPU): every rank runs its own grid (replicas,
+weak scaling, no collective on the data path); value = all ranks' lattice-site
+updates / max-over-ranks time.  --impl reference times the CPU oracle (the
+reference statement of the method) on the host cores on a bounded sample of the
+same workload.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+NX = NY = NZ = 512
+NSWEEPS = 100
+DP_OPS_PER_LUP = 6          # 5 adds + 1 multiply (Eq. 1)
+SM_COUNT = 152
+DP_OPS_PER_CLK_PER_SM = 2   # GB300 FP64: 1.25 TFLOP/s nominal with FMA counted as 2
+ALGO_BYTES_PER_LUP = {"f64": 16, "f32": 8, "bf16": 4}
+
+# DRAM bytes per launch of the dominant kernel from the ncu captures committed
+# under profiles/ (None when no capture of the current kernel exists).
+TRAFFIC_PER_LAUNCH = {}
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--t", type=int, default=0, help="temporal-blocking depth (0: planner)")
+    p.add_argument("--no-variants", action="store_true", help="skip the extra rows")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--case", default="", help="profiling case: run only one kernel "
+                   "configuration, e.g. --case sweep --dtype f32 --kernel tb --t 4 --size 384")
+    p.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
+    p.add_argument("--kernel", default="auto", choices=["auto", "plain", "tb"])
+    p.add_argument("--size", type=int, default=NX)
+    p.add_argument("--sweeps", type=int, default=NSWEEPS)
+    return p.parse_args()
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks/throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.out = os.path.join("/tmp", f"jacobi_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.out, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        rows = []
+        with open(self.out) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.out)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[4:8]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def make_input(dtype="f64"):
+    from paper_0912_4506_gb300 import inputs
+    a = inputs.uniform_grid_f64(NX, NY, NZ, px=inputs.row_pitch(NX, dtype))
+    return a if dtype == "f64" else inputs.to_dtype(a, dtype)
+
+
+def cpu_oracle_rate(a64, budget_s=12.0, max_sweeps=100):
+    """Time the CPU oracle (as it stands, OpenMP over k on every host core) on
+    the 512^3 FP64 grid; returns (GLUP/s, cores, sample description)."""
+    import oracle
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    oracle.sweeps(a64, 1, nx=NX, nthreads=cores)
+    one = time.perf_counter() - t0
+    n = int(max(1, min(max_sweeps, budget_s / max(one, 1e-6))))
+    t0 = time.perf_counter()
+    oracle.sweeps(a64, n, nx=NX, nthreads=cores)
+    dt = time.perf_counter() - t0
+    rate = NX * NY * NZ * n / dt / 1e9
+    return rate, cores, f"{n} sweeps of the 512^3 FP64 grid (same seeds), {dt:.1f} s"
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    a64 = make_input("f64")
+    cores = os.cpu_count() or 1
+    per_step = 8
+    for _ in range(args.warmup):
+        oracle.sweeps(a64, per_step, nx=NX, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sweeps(a64, per_step, nx=NX, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = NX * NY * NZ * per_step * args.steps / dt / 1e9
+    line = {
+        "impl": "reference", "metric": "GLUP/s, 512^3 FP64 7-point Jacobi", "value": value,
+        "unit": "GLUP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "jacobi7pt_512^3_fp64", "nx": NX, "ny": NY, "nz": NZ,
+                   "sweeps_per_step": per_step, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{per_step} sweeps of the 512^3 FP64 grid per step"},
+        "e2e": {"value": value, "unit": "GLUP/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+def time_sweeps(j, nsweeps, t, kernel, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        j.sweep(nsweeps, t, kernel)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        j.sweep(nsweeps, t, kernel)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+def variant_rows(dev, steps):
+    """GLUP/s of the other paths on the same GPU (beside the plain FP64 form)."""
+    import torch
+    from paper_0912_4506_gb300 import api
+    rows = {}
+    stream = torch.cuda.current_stream()
+    for dtype in ("f64", "f32", "bf16"):
+        j = api.Jacobi(api.from_numpy(make_input(dtype), NX, dev))
+        tmax = 4 if dtype == "f64" else 8
+        for t, kern, name in [(1, api.JAC_KERNEL_PLAIN, "plain")] + \
+                [(t, api.JAC_KERNEL_TB, f"tb_t{t}") for t in (1, 2, 4, 8, 16)
+                 if t <= tmax or dtype == "f64"]:
+            ms = time_sweeps(j, NSWEEPS, t, kern, steps, 1, stream)
+            plan = j.plan(NSWEEPS, t, kern)
+            rows[f"{dtype}_{name}"] = {
+                "glups": round(NX * NY * NZ * NSWEEPS / ms / 1e6, 2),
+                "ms_per_100_sweeps": round(ms, 3), "t_used": plan["t"],
+                "remainder_t": plan["remainder_t"]}
+        j.close()
+        del j
+        torch.cuda.empty_cache()
+    return rows
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_0912_4506_gb300 import api
+
+    a64 = make_input("f64")
+    j = api.Jacobi(api.from_numpy(a64, NX, dev))
+    stream = torch.cuda.current_stream(dev)
+    plan = j.plan(NSWEEPS, args.t, api.JAC_KERNEL_AUTO)
+    launches_per_step = plan["passes"]
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        j.sweep(NSWEEPS, args.t)
+    torch.cuda.synchronize()
+    barrier()
+    gpu_uuid = torch.cuda.get_device_properties(dev).uuid
+    sampler = ClockSampler(f"GPU-{gpu_uuid}" if gpu_uuid else local)
+    sampler.start()
+    time.sleep(0.3)
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        j.sweep(NSWEEPS, args.t)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+    ms_step = ms / args.steps
+    lups = NX * NY * NZ * NSWEEPS
+    value = lups * world / (ms_step / 1e3) / 1e9
+
+    # end to end through the C ABI on host buffers: upload, 100 sweeps, download
+    host_in = torch.from_numpy(a64).pin_memory()
+    host_out = torch.empty_like(host_in).pin_memory()
+    j.run_host(host_in, host_out, NSWEEPS, args.t)
+    torch.cuda.synchronize()
+    barrier()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        j.run_host(host_in, host_out, NSWEEPS, args.t)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms_e2e = e2.elapsed_time(e3)
+    if world > 1:
+        tt = torch.tensor([ms_e2e], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms_e2e = float(tt.item())
+    e2e_value = lups * world / (ms_e2e / args.steps / 1e3) / 1e9
+    nbytes = host_in.numel() * host_in.element_size()
+
+    if rank != 0:
+        j.close()
+        return
+
+    pk, pk_src = peaks()
+    kname = "plain_sweep_kernel<F64>" if plan["kernel"] == 1 else f"tb_sweep_kernel<F64,T={plan['t']}>"
+    launch_s = ms_step / 1e3 / launches_per_step
+    sweeps_per_launch = NSWEEPS / launches_per_step
+    if plan["kernel"] == 1:
+        mhz = pk.get("sm_max_mhz", 2070.0)
+        peak_tf = DP_OPS_PER_CLK_PER_SM * SM_COUNT * mhz * 1e6 / 1e12
+        achieved = DP_OPS_PER_LUP * NX * NY * NZ * sweeps_per_launch / launch_s / 1e12
+        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tf, 4),
+                "unit": "TFLOP/s", "frac": round(achieved / peak_tf, 4),
+                "traffic": TRAFFIC_PER_LAUNCH.get(kname),
+                "kernel": kname,
+                "peak_source": f"FP64 pipe: {DP_OPS_PER_CLK_PER_SM} DP ops/clk/SM x "
+                               f"{SM_COUNT} SMs x {mhz:.0f} MHz (derived from unit counts and "
+                               "the maximum SM clock)",
+                "hbm_frac": round(ALGO_BYTES_PER_LUP["f64"] * NX * NY * NZ * sweeps_per_launch
+                                  / launch_s / 1e9 / pk["hbm_gbs"], 4)}
+    else:
+        bytes_launch = ALGO_BYTES_PER_LUP["f64"] * NX * NY * NZ
+        achieved = bytes_launch / launch_s / 1e9
+        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
+                "traffic": TRAFFIC_PER_LAUNCH.get(kname), "kernel": kname,
+                "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({pk_src})"}
+    roof["launch_ms"] = round(launch_s * 1e3, 4)
+
+    line = {
+        "metric": "GLUP/s, 512^3 FP64 7-point Jacobi (100 sweeps A->B->A)",
+        "value": round(value, 3), "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "jacobi7pt_512^3_fp64_100sweeps", "nx": NX, "ny": NY, "nz": NZ,
+                   "sweeps_per_step": NSWEEPS, "plan": plan,
+                   "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (1.09 GB per grid), no flush"},
+        "roofline": roof,
+        "gpu_launches": launches_per_step * args.steps,
+        "e2e": {"value": round(e2e_value, 3), "unit": "GLUP/s",
+                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes},
+        "clocks": clocks,
+        "peaks": pk_src,
+    }
+    j.close()
+    del j
+    torch.cuda.empty_cache()
+    if world == 1 and not args.no_variants:
+        line["variants"] = variant_rows(dev, max(2, min(args.steps, 3)))
+    if world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate(a64)
+        line["cpu_baseline"] = {"value": round(rate, 4), "unit": "GLUP/s", "cores": cores,
+                                "kind": "oracle", "sample": sample}
+    print(json.dumps(line), flush=True)
+
+
+def run_case(args):
+    """One kernel configuration only (for profiler captures): args.steps calls of
+    args.sweeps sweeps on a size^3 grid of args.dtype."""
+    import torch
+    from paper_0912_4506_gb300 import api, inputs
+    n = args.size
+    a = inputs.to_dtype(inputs.uniform_grid_f64(n, n, n), args.dtype,
+                        px=inputs.row_pitch(n, args.dtype))
+    j = api.Jacobi(api.from_numpy(a, n, "cuda"))
+    kern = {"auto": api.JAC_KERNEL_AUTO, "plain": api.JAC_KERNEL_PLAIN,
+            "tb": api.JAC_KERNEL_TB}[args.kernel]
+    ms = time_sweeps(j, args.sweeps, args.t, kern, args.steps, args.warmup,
+                     torch.cuda.current_stream())
+    j.check()
+    print(json.dumps({"case": args.case, "dtype": args.dtype, "kernel": args.kernel,
+                      "t": args.t, "size": n, "sweeps": args.sweeps, "ms": round(ms, 4),
+                      "glups": round(n ** 3 * args.sweeps / ms / 1e6, 2),
+                      "plan": j.plan(args.sweeps, args.t, kern)}), flush=True)
+    j.close()
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.case:
+        run_case(a)
+    elif a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -163,6 +163,17 @@ JAC_API int jacobi_residual_accumulate(int nx, int ny, int nz, const double *u_i
 JAC_API int jacobi_adjoint(jacobi_t h, void *grad_bdry, int nsweeps, int t,
                    int *final_is_b);
 
+/*
+ * jacobi_upload / jacobi_download — copy a whole padded grid between host memory
+ * and the handle's grid A (upload) or the grid holding a result (download,
+ * from_b = the final_is_b of the sweep call), asynchronously on the handle's
+ * stream.  host: (nz+2)*(ny+2)*row_pitch elements, same layout as the device
+ * grids; page-locked memory makes the copy asynchronous, pageable memory works
+ * but synchronises.  Upload also refreshes B's boundary layer from A.
+ */
+JAC_API int jacobi_upload(jacobi_t h, const void *host);
+JAC_API int jacobi_download(jacobi_t h, void *host, int from_b);
+
 /* jacobi_check — wait for the handle's stream and report a device-side status
  * (JAC_ETIMEOUT when a bounded wait ran out) or a CUDA error (JAC_ECUDA).  The
  * status word is cleared. */

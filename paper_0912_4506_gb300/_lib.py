@@ -14,7 +14,8 @@ JAC_KERNEL_AUTO, JAC_KERNEL_PLAIN, JAC_KERNEL_TB = 0, 1, 2
 
 EXPORTS = ["jacobi_create", "jacobi_sweep", "jacobi_sweep_ex", "jacobi_plan",
            "jacobi_sweep_rhs", "jacobi_residual_accumulate", "jacobi_adjoint",
-           "jacobi_check", "jacobi_destroy", "jacobi_strerror", "jacobi_version"]
+           "jacobi_upload", "jacobi_download", "jacobi_check", "jacobi_destroy",
+           "jacobi_strerror", "jacobi_version"]
 
 
 class JacobiError(RuntimeError):
@@ -55,6 +56,8 @@ def load(path=None):
         "jacobi_sweep_rhs": ([P, P, I, I, PI], I),
         "jacobi_residual_accumulate": ([I, I, I, P, P, LL, P, P, I, LL, P], I),
         "jacobi_adjoint": ([P, P, I, I, PI], I),
+        "jacobi_upload": ([P, P], I),
+        "jacobi_download": ([P, P, I], I),
         "jacobi_check": ([P], I),
         "jacobi_destroy": ([P], I),
         "jacobi_strerror": ([I], ctypes.c_char_p),
@@ -119,6 +122,14 @@ def jacobi_adjoint(h, grad_bdry, nsweeps, t=0):
     fb = ctypes.c_int(0)
     _ck(load().jacobi_adjoint(h, grad_bdry, nsweeps, t, ctypes.byref(fb)), "jacobi_adjoint")
     return fb.value
+
+
+def jacobi_upload(h, host_ptr):
+    _ck(load().jacobi_upload(h, host_ptr), "jacobi_upload")
+
+
+def jacobi_download(h, host_ptr, from_b):
+    _ck(load().jacobi_download(h, host_ptr, from_b), "jacobi_download")
 
 
 def jacobi_check(h):

@@ -47,6 +47,18 @@ def as_grid(full, nx):
     return full[:, :, :nx + 2]
 
 
+def from_numpy(a, nx, device="cuda"):
+    """Grid view (interior width nx) of a host array of shape (nz+2, ny+2,
+    row_pitch): float64/float32 arrays, or uint16 arrays holding bf16 bits."""
+    import numpy as np
+    if a.dtype == np.uint16:
+        t = torch.from_numpy(np.ascontiguousarray(a).view(np.int16)).to(device)
+        t = t.view(torch.bfloat16)
+    else:
+        t = torch.from_numpy(np.ascontiguousarray(a)).to(device)
+    return as_grid(t, nx)
+
+
 def _stream_ptr(device=None):
     return torch.cuda.current_stream(device).cuda_stream
 
@@ -110,6 +122,27 @@ class Jacobi:
         with torch.cuda.device(self.device):
             fb = _lib.jacobi_adjoint(self._h, grad_bdry.data_ptr(), nsweeps, t)
         return self.B if fb else self.A
+
+    def upload(self, host):
+        """Copy a host grid (a pinned CPU tensor of A's full padded storage shape
+        (nz+2, ny+2, row_pitch)) into A, asynchronously on the handle's stream."""
+        with torch.cuda.device(self.device):
+            _lib.jacobi_upload(self._h, host.data_ptr())
+
+    def download(self, host, from_b):
+        """Copy A (from_b=0) or B (from_b=1) into a host tensor of the full padded
+        storage shape, asynchronously on the handle's stream."""
+        with torch.cuda.device(self.device):
+            _lib.jacobi_download(self._h, host.data_ptr(), int(from_b))
+
+    def run_host(self, host_in, host_out, nsweeps, t=0, kernel=JAC_KERNEL_AUTO):
+        """Upload, sweep, download: the end-to-end call on host buffers.  Returns
+        after enqueueing; synchronise the stream before reading host_out."""
+        self.upload(host_in)
+        with torch.cuda.device(self.device):
+            fb = _lib.jacobi_sweep_ex(self._h, nsweeps, t, kernel)
+        self.download(host_out, fb)
+        return fb
 
     def plan(self, nsweeps, t=0, kernel=JAC_KERNEL_AUTO):
         with torch.cuda.device(self.device):
@@ -205,5 +238,5 @@ def refine_solve(u0, outer, inner, dtype="f32", t=0):
 
 
 __all__ = ["Jacobi", "Refiner", "sweep", "residual_accumulate", "refine_solve", "alloc_grid",
-           "alloc_like", "as_grid", "grid_geom", "row_pitch", "JacobiError",
+           "alloc_like", "as_grid", "from_numpy", "grid_geom", "row_pitch", "JacobiError",
            "JAC_KERNEL_AUTO", "JAC_KERNEL_PLAIN", "JAC_KERNEL_TB"]

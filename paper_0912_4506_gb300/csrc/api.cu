@@ -406,6 +406,29 @@ int jacobi_residual_accumulate(int nx, int ny, int nz, const double* u_in, doubl
     return JAC_OK;
 }
 
+static size_t grid_bytes(const jacobi_s* h) {
+    return (size_t)h->g.plane * (size_t)(h->g.nz + 2) * (size_t)elem_size(h->dtype);
+}
+
+int jacobi_upload(jacobi_t h, const void* host) {
+    if (!h || !host) return JAC_EINVAL;
+    if (cudaSetDevice(h->device) != cudaSuccess) return JAC_ECUDA;
+    if (cudaMemcpyAsync(h->a, host, grid_bytes(h), cudaMemcpyHostToDevice, h->stream) !=
+            cudaSuccess ||
+        launch_boundary_copy(h->dtype, h->a, h->b, h->g, h->stream) != cudaSuccess)
+        return JAC_ECUDA;
+    return JAC_OK;
+}
+
+int jacobi_download(jacobi_t h, void* host, int from_b) {
+    if (!h || !host) return JAC_EINVAL;
+    if (cudaSetDevice(h->device) != cudaSuccess) return JAC_ECUDA;
+    if (cudaMemcpyAsync(host, from_b ? h->b : h->a, grid_bytes(h), cudaMemcpyDeviceToHost,
+                        h->stream) != cudaSuccess)
+        return JAC_ECUDA;
+    return JAC_OK;
+}
+
 int jacobi_check(jacobi_t h) {
     if (!h) return JAC_EINVAL;
     if (cudaSetDevice(h->device) != cudaSuccess) return JAC_ECUDA;

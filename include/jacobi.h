@@ -174,6 +174,38 @@ JAC_API int jacobi_adjoint(jacobi_t h, void *grad_bdry, int nsweeps, int t,
 JAC_API int jacobi_upload(jacobi_t h, const void *host);
 JAC_API int jacobi_download(jacobi_t h, void *host, int from_b);
 
+/*
+ * jacobi_sweep_noalloc — jacobi_sweep for callers that cannot allocate device
+ * memory: code running where cudaMalloc is not allowed or not wanted, such as a
+ * host framework that owns every device byte through its own pool, a plug-in
+ * that must not grow the process's device footprint, or code being recorded
+ * into a CUDA graph.  There is no counterpart in the paper; it is a deployment
+ * convenience.  No handle is needed and nothing is allocated: the second
+ * (ping-pong) grid and the device status word live in one static device array
+ * of JAC_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that
+ * loads the library keeps until the process exits.
+ *   grid       the caller's device grid (layout as above): input on entry,
+ *              result on return (the library copies the result back when the
+ *              last pass ends in the scratch grid).  Row padding is not touched.
+ *   nsweeps, t as in jacobi_sweep.
+ *   stream     cudaStream_t (NULL: legacy default stream).
+ *   sync       0: return after enqueueing; nonzero: wait for the stream and
+ *              report a device-side timeout as JAC_ETIMEOUT.
+ * The padded grid, (nz+2)*(ny+2)*row_pitch elements, must fit in
+ * JAC_NOALLOC_SCRATCH_BYTES - 256 bytes (about 4.1 M FP64 or 8.4 M FP32 cells);
+ * larger grids are rejected with JAC_EINVAL before anything runs.
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  Every call shares the one scratch array, which keeps the
+ * previous call's contents (each call re-initialises what it needs): calls
+ * that can overlap on the GPU (different streams, or different threads) race,
+ * so serialise them.
+ */
+#define JAC_NOALLOC_SCRATCH_BYTES (32u << 20)
+JAC_API int jacobi_sweep_noalloc(int nx, int ny, int nz, int dtype, void *grid,
+                                 long long row_pitch, int nsweeps, int t, void *stream,
+                                 int sync);
+
 /* jacobi_check — wait for the handle's stream and report a device-side status
  * (JAC_ETIMEOUT when a bounded wait ran out) or a CUDA error (JAC_ECUDA).  The
  * status word is cleared. */

@@ -15,7 +15,7 @@ JAC_KERNEL_AUTO, JAC_KERNEL_PLAIN, JAC_KERNEL_TB = 0, 1, 2
 EXPORTS = ["jacobi_create", "jacobi_sweep", "jacobi_sweep_ex", "jacobi_plan",
            "jacobi_sweep_rhs", "jacobi_residual_accumulate", "jacobi_adjoint",
            "jacobi_upload", "jacobi_download", "jacobi_check", "jacobi_destroy",
-           "jacobi_strerror", "jacobi_version"]
+           "jacobi_strerror", "jacobi_version", "jacobi_sweep_noalloc"]
 
 
 class JacobiError(RuntimeError):
@@ -62,6 +62,7 @@ def load(path=None):
         "jacobi_destroy": ([P], I),
         "jacobi_strerror": ([I], ctypes.c_char_p),
         "jacobi_version": ([], I),
+        "jacobi_sweep_noalloc": ([I, I, I, I, P, LL, I, I, P, I], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -142,3 +143,10 @@ def jacobi_destroy(h):
 
 def jacobi_version():
     return load().jacobi_version()
+
+
+def jacobi_sweep_noalloc(nx, ny, nz, dtype, grid, row_pitch, nsweeps, t, stream, sync):
+    """Sweep that allocates nothing (the library's static scratch holds the second
+    grid); the result is left in ``grid``."""
+    _ck(load().jacobi_sweep_noalloc(nx, ny, nz, dtype, grid, row_pitch, nsweeps, t, stream,
+                                    sync), "jacobi_sweep_noalloc")

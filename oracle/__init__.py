@@ -121,6 +121,7 @@ def residual_accumulate(u, e, nx=None, dtype="f32", lib=None):
     lib = lib or load()
     u = np.ascontiguousarray(u, dtype=np.float64).copy()
     e = np.ascontiguousarray(e, dtype=_DT[dtype])
+    assert e.shape == u.shape, "u and e must share the padded shape (row pitch included)"
     nx = u.shape[2] - 2 if nx is None else nx
     ny, nz, px, py = _dims(u, nx)
     rho = np.zeros_like(e)

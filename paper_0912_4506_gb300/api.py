@@ -237,6 +237,85 @@ def refine_solve(u0, outer, inner, dtype="f32", t=0):
     return out
 
 
-__all__ = ["Jacobi", "Refiner", "sweep", "residual_accumulate", "refine_solve", "alloc_grid",
+__all__ = ["Jacobi", "JacobiFn", "jacobi_fn", "Refiner", "sweep", "residual_accumulate", "refine_solve", "alloc_grid",
            "alloc_like", "as_grid", "from_numpy", "grid_geom", "row_pitch", "JacobiError",
            "JAC_KERNEL_AUTO", "JAC_KERNEL_PLAIN", "JAC_KERNEL_TB"]
+
+
+class JacobiFn(torch.autograd.Function):
+    """Differentiable n-sweep Jacobi map: Y = n temporally-blocked sweeps of X.
+
+    X is a grid (interior = initial values, boundary layer = Dirichlet data g).
+    The backward pass runs the library's adjoint sweeps: lambda_n = dL/dY on the
+    interior (zero boundary), n transpose sweeps (the same stencil on a zero
+    boundary, the sweep being symmetric on the interior), while the boundary
+    gradient accumulates RN(1/6)*lambda_s at each face cell's interior neighbour,
+    plus the direct dL/dY on the boundary layer (Y's boundary is g).  Returns one
+    grid: interior dL/dX_interior, boundary layer dL/dg.
+
+    With ``checkpoint=True`` the forward pass keeps the state after every pass of
+    depth t in ``ctx.checkpoints`` (a list of grids).  The sweep map is affine in
+    (X, g), so the backward pass needs no forward state: the gradients are the
+    same with and without checkpoints.
+    """
+
+    @staticmethod
+    def forward(ctx, X, nsweeps, t=0, checkpoint=False):
+        if X.dtype not in (torch.float32, torch.float64):
+            raise ValueError("JacobiFn supports float32 and float64 grids")
+        A = alloc_like(X)
+        A.copy_(X)
+        j = Jacobi(A)
+        ckpts = []
+        if checkpoint and nsweeps > 0:
+            step = t if t > 0 else 4
+            done = 0
+            while done < nsweeps:
+                d = min(step, nsweeps - done)
+                out = j.sweep(d, d, JAC_KERNEL_TB)
+                if out is j.B:
+                    j.A.copy_(j.B)
+                c = alloc_like(X)
+                c.copy_(j.A)
+                ckpts.append(c)
+                done += d
+            Y = j.A
+        else:
+            Y = j.sweep(nsweeps, t, JAC_KERNEL_TB if nsweeps else JAC_KERNEL_AUTO)
+        j.close()
+        ctx.nsweeps, ctx.t = nsweeps, t
+        ctx.checkpoints = ckpts
+        Yc = alloc_like(X)
+        Yc.copy_(Y)
+        return Yc
+
+    @staticmethod
+    def backward(ctx, gY):
+        gY = gY.to(torch.float64 if gY.dtype == torch.float64 else torch.float32)
+        lam = alloc_like(gY) if _is_grid(gY) else None
+        if lam is None:  # gradient arrived densely laid out: re-pad it
+            nz2, ny2, nx2 = gY.shape
+            lam = alloc_grid(nx2 - 2, ny2 - 2, nz2 - 2, gY.dtype, gY.device)
+        lam[1:-1, 1:-1, 1:-1].copy_(gY[1:-1, 1:-1, 1:-1])
+        grad = alloc_like(lam)
+        grad.copy_(gY)
+        grad[1:-1, 1:-1, 1:-1].zero_()
+        j = Jacobi(lam)
+        out = j.adjoint(grad, ctx.nsweeps, ctx.t)
+        j.check()
+        grad[1:-1, 1:-1, 1:-1].copy_(out[1:-1, 1:-1, 1:-1])
+        j.close()
+        return grad, None, None, None
+
+
+def _is_grid(t):
+    try:
+        grid_geom(t)
+        return True
+    except ValueError:
+        return False
+
+
+def jacobi_fn(X, nsweeps, t=0, checkpoint=False):
+    """Autograd-aware n-sweep Jacobi map (see JacobiFn)."""
+    return JacobiFn.apply(X, nsweeps, t, checkpoint)

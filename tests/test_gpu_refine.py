@@ -1,0 +1,86 @@
+"""GPU parity of the mixed-precision refinement pieces against the CPU oracle:
+correction sweeps (FP32 and bf16 storage, every depth), the FP64 residual step,
+and the whole refinement driver (all bit-exact: same operations, same order)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0912_4506_gb300 import inputs
+from tests.helpers import NP_DT, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _rand_interior(nx, ny, nz, dtype, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    px = inputs.row_pitch(nx, dtype)
+    a = np.zeros((nz + 2, ny + 2, px), dtype=np.float64)
+    a[1:-1, 1:-1, 1:nx + 1] = (rng.random((nz, ny, nx)) - 0.5) * scale
+    return inputs.to_dtype(a, dtype, px=px)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+@pytest.mark.parametrize("shape", [(45, 38, 17), (64, 64, 64), (3, 70, 5)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_rhs_sweeps_bit_exact(dtype, shape):
+    from paper_0912_4506_gb300 import api
+    nx, ny, nz = shape
+    e = _rand_interior(nx, ny, nz, dtype, 1)
+    rho = _rand_interior(nx, ny, nz, dtype, 2, scale=0.1)
+    for n in (1, 7, 13):
+        want = oracle.rhs_sweeps(e, rho, n, nx=nx, dtype=dtype)[:, :, :nx + 2]
+        for t in (1, 2, 3, 4, 5, 8):
+            j = api.Jacobi(api.as_grid(to_dev(e, dtype), nx))
+            out = j.sweep_rhs(api.as_grid(to_dev(rho, dtype), nx), n, t)
+            j.check()
+            got = to_host(out, dtype)
+            j.close()
+            assert np.array_equal(got, want), (n, t)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_residual_accumulate_bit_exact(dtype):
+    from paper_0912_4506_gb300 import api
+    nx, ny, nz = 53, 41, 19
+    u = inputs.uniform_grid_f64(nx, ny, nz, px=inputs.row_pitch(nx, "f64")) * 100.0 - 50.0
+    e = _rand_interior(nx, ny, nz, dtype, 3, scale=1e-3)
+    e_same = np.zeros(u.shape, dtype=e.dtype)  # the oracle takes one row pitch for both
+    w = min(u.shape[2], e.shape[2])
+    e_same[:, :, :w] = e[:, :, :w]
+    want_u, want_rho = oracle.residual_accumulate(u, e_same, nx=nx, dtype=dtype)
+    ug = api.as_grid(to_dev(u, "f64"), nx)
+    uo = api.alloc_like(ug)
+    uo.copy_(ug)
+    eg = api.as_grid(to_dev(e, dtype), nx)
+    rho = api.alloc_like(eg)
+    api.residual_accumulate(ug, uo, eg, rho)
+    got_u = to_host(uo, "f64")
+    got_rho = to_host(rho, dtype)
+    assert np.array_equal(got_u, want_u[:, :, :nx + 2])
+    assert np.array_equal(got_rho[1:-1, 1:-1, 1:-1], want_rho[1:-1, 1:-1, 1:nx + 1])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_refine_solve_bit_exact(dtype):
+    """Laplace problem (boundary u = x^2 - y^2 + 0.5 z, zero interior): 3 outer
+    steps of 7 correction sweeps, GPU vs oracle, bit for bit."""
+    from paper_0912_4506_gb300 import api
+    nx, ny, nz = 40, 30, 22
+    u0 = inputs.laplace_boundary_f64(nx, ny, nz, px=inputs.row_pitch(nx, "f64"))
+    want = oracle.refine_solve(u0, 3, 7, dtype=dtype)[:, :, :nx + 2]
+    for t in (0, 3, 7):
+        got = to_host(api.refine_solve(api.as_grid(to_dev(u0, "f64"), nx), 3, 7, dtype, t),
+                      "f64")
+        assert np.array_equal(got, want), t
+
+
+def test_refinement_tracks_fp64_sweeps():
+    """Exact arithmetic makes O outer x m inner refinement equal O*m FP64 sweeps;
+    in FP32 storage the difference stays at FP32 rounding size."""
+    from paper_0912_4506_gb300 import api
+    nx, ny, nz = 48, 40, 36
+    u0 = inputs.laplace_boundary_f64(nx, ny, nz, px=inputs.row_pitch(nx, "f64"))
+    plain = to_host(api.sweep(api.as_grid(to_dev(u0, "f64"), nx), 60, 1), "f64")
+    ir = to_host(api.refine_solve(api.as_grid(to_dev(u0, "f64"), nx), 4, 15, "f32"), "f64")
+    scale = np.abs(u0).max()
+    assert np.abs(ir - plain).max() <= 4 * 60 * 2.0 ** -24 * scale

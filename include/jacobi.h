@@ -175,6 +175,55 @@ JAC_API int jacobi_upload(jacobi_t h, const void *host);
 JAC_API int jacobi_download(jacobi_t h, void *host, int from_b);
 
 /*
+ * Batched grids: many independent grids (different shapes, sweep counts and
+ * depths) advanced by one persistent kernel launch, recorded once into a CUDA
+ * graph and replayed by jacobi_batch_run.  Every grid's sweeps are the same
+ * bit-exact sweeps as jacobi_sweep with the same depth.
+ */
+typedef struct jacobi_batch_s *jacobi_batch_t;
+
+#define JAC_BATCH_NO_GRAPH 1               /* launch directly instead of a CUDA graph  */
+#define JAC_BATCH_TEST_MISSING_PRODUCER 2  /* test hook: add one work item that waits
+                                              for a tile no item produces, so the run
+                                              ends in JAC_ETIMEOUT (bounded wait)      */
+
+/*
+ * jacobi_batch_create — plan a batch of `count` grids of one dtype (JAC_F32 or
+ * JAC_BF16).  Per grid i: dims[3i..3i+2] = (nx, ny, nz), pitches[i] = row pitch
+ * (elements, row a multiple of 16 bytes), grids_a[i]/grids_b[i] = caller-owned
+ * device grids (A holds the initial grid and boundary layer; B receives A's
+ * boundary layer here), nsweeps[i] >= 0, t[i] = depth (0 or t == NULL: 4;
+ * at most 6), nchunk[i] = k-chunks per pass (0 or nchunk == NULL: planner).
+ * Work items are (grid, pass, tile) in pass-round order; a CTA waits (bounded by
+ * wait_limit_s, 0 = 2 s) for the previous pass of its grid.  The library owns the
+ * descriptors, the work list and the counters (freed by jacobi_batch_destroy).
+ */
+JAC_API int jacobi_batch_create(jacobi_batch_t *out, int count, const int *dims,
+                                const long long *pitches, void *const *grids_a,
+                                void *const *grids_b, const int *nsweeps, const int *t,
+                                const int *nchunk, int dtype, void *stream, int flags,
+                                double wait_limit_s);
+
+/* jacobi_batch_run — enqueue one run of the whole batch on the batch's stream
+ * (every grid advances by its own sweep count from A).  final_is_b (count
+ * entries, may be NULL) reports per grid whether the result is in B.  A run
+ * starts from the current contents of each A, so a second run continues from
+ * wherever the first left A (the result itself when it ended in A). */
+JAC_API int jacobi_batch_run(jacobi_batch_t b, int *final_is_b);
+
+/* jacobi_batch_info — per grid: depth used and number of passes; totals: work
+ * items and persistent CTAs.  Any pointer may be NULL. */
+JAC_API int jacobi_batch_info(jacobi_batch_t b, int *t_used, int *passes, int *items,
+                              int *ctas);
+
+/* jacobi_batch_check — wait for the batch's stream; JAC_ETIMEOUT if a bounded
+ * device wait ran out during a run. */
+JAC_API int jacobi_batch_check(jacobi_batch_t b);
+
+/* jacobi_batch_destroy — release the batch (not the grids).  NULL is accepted. */
+JAC_API int jacobi_batch_destroy(jacobi_batch_t b);
+
+/*
  * jacobi_sweep_noalloc — jacobi_sweep for callers that cannot allocate device
  * memory: code running where cudaMalloc is not allowed or not wanted, such as a
  * host framework that owns every device byte through its own pool, a plug-in

@@ -15,7 +15,11 @@ JAC_KERNEL_AUTO, JAC_KERNEL_PLAIN, JAC_KERNEL_TB = 0, 1, 2
 EXPORTS = ["jacobi_create", "jacobi_sweep", "jacobi_sweep_ex", "jacobi_plan",
            "jacobi_sweep_rhs", "jacobi_residual_accumulate", "jacobi_adjoint",
            "jacobi_upload", "jacobi_download", "jacobi_check", "jacobi_destroy",
-           "jacobi_strerror", "jacobi_version", "jacobi_sweep_noalloc"]
+           "jacobi_strerror", "jacobi_version", "jacobi_sweep_noalloc",
+           "jacobi_batch_create", "jacobi_batch_run", "jacobi_batch_info", "jacobi_batch_check",
+           "jacobi_batch_destroy"]
+
+JAC_BATCH_NO_GRAPH, JAC_BATCH_TEST_MISSING_PRODUCER = 1, 2
 
 
 class JacobiError(RuntimeError):
@@ -63,6 +67,12 @@ def load(path=None):
         "jacobi_strerror": ([I], ctypes.c_char_p),
         "jacobi_version": ([], I),
         "jacobi_sweep_noalloc": ([I, I, I, I, P, LL, I, I, P, I], I),
+        "jacobi_batch_create": ([ctypes.POINTER(P), I, PI, ctypes.POINTER(LL), ctypes.POINTER(P),
+                                 ctypes.POINTER(P), PI, PI, PI, I, P, I, ctypes.c_double], I),
+        "jacobi_batch_run": ([P, PI], I),
+        "jacobi_batch_info": ([P, PI, PI, PI, PI], I),
+        "jacobi_batch_check": ([P], I),
+        "jacobi_batch_destroy": ([P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -150,3 +160,47 @@ def jacobi_sweep_noalloc(nx, ny, nz, dtype, grid, row_pitch, nsweeps, t, stream,
     grid); the result is left in ``grid``."""
     _ck(load().jacobi_sweep_noalloc(nx, ny, nz, dtype, grid, row_pitch, nsweeps, t, stream,
                                     sync), "jacobi_sweep_noalloc")
+
+
+def _ints(v):
+    return (ctypes.c_int * len(v))(*v)
+
+
+def jacobi_batch_create(dims, pitches, grids_a, grids_b, nsweeps, t, nchunk, dtype, stream,
+                        flags=0, wait_limit_s=0.0):
+    """dims: list of (nx, ny, nz); the other lists have one entry per grid."""
+    n = len(dims)
+    h = ctypes.c_void_p()
+    flat = [int(x) for d in dims for x in d]
+    P = ctypes.c_void_p
+    rc = load().jacobi_batch_create(
+        ctypes.byref(h), n, _ints(flat), (ctypes.c_longlong * n)(*pitches),
+        (P * n)(*grids_a), (P * n)(*grids_b), _ints(nsweeps),
+        _ints(t) if t is not None else None, _ints(nchunk) if nchunk is not None else None,
+        dtype, stream, flags, float(wait_limit_s))
+    _ck(rc, "jacobi_batch_create")
+    return h
+
+
+def jacobi_batch_run(h, count):
+    fb = (ctypes.c_int * count)()
+    _ck(load().jacobi_batch_run(h, fb), "jacobi_batch_run")
+    return list(fb)
+
+
+def jacobi_batch_info(h, count):
+    t = (ctypes.c_int * count)()
+    p = (ctypes.c_int * count)()
+    items = ctypes.c_int(0)
+    ctas = ctypes.c_int(0)
+    _ck(load().jacobi_batch_info(h, t, p, ctypes.byref(items), ctypes.byref(ctas)),
+        "jacobi_batch_info")
+    return {"t": list(t), "passes": list(p), "items": items.value, "ctas": ctas.value}
+
+
+def jacobi_batch_check(h):
+    _ck(load().jacobi_batch_check(h), "jacobi_batch_check")
+
+
+def jacobi_batch_destroy(h):
+    _ck(load().jacobi_batch_destroy(h), "jacobi_batch_destroy")

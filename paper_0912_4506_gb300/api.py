@@ -237,7 +237,7 @@ def refine_solve(u0, outer, inner, dtype="f32", t=0):
     return out
 
 
-__all__ = ["Jacobi", "JacobiFn", "jacobi_fn", "Refiner", "sweep", "residual_accumulate", "refine_solve", "alloc_grid",
+__all__ = ["Jacobi", "JacobiFn", "jacobi_fn", "Batch", "Refiner", "sweep", "residual_accumulate", "refine_solve", "alloc_grid",
            "alloc_like", "as_grid", "from_numpy", "grid_geom", "row_pitch", "JacobiError",
            "JAC_KERNEL_AUTO", "JAC_KERNEL_PLAIN", "JAC_KERNEL_TB"]
 
@@ -319,3 +319,59 @@ def _is_grid(t):
 def jacobi_fn(X, nsweeps, t=0, checkpoint=False):
     """Autograd-aware n-sweep Jacobi map (see JacobiFn)."""
     return JacobiFn.apply(X, nsweeps, t, checkpoint)
+
+
+class Batch:
+    """Many independent grids advanced together by one persistent kernel launch,
+    recorded into a CUDA graph (include/jacobi.h, jacobi_batch_*).
+
+    ``grids``: list of float32 or bfloat16 grids (each its own shape); ``nsweeps``:
+    sweeps per grid; ``t``: depth per grid (None: 4, or the autotuner's choice);
+    ``nchunk``: k-chunks per pass per grid (None: planner).  B grids are allocated
+    with each A's layout.  ``run()`` returns the list of tensors holding the
+    results.
+    """
+
+    def __init__(self, grids, nsweeps, t=None, nchunk=None, graph=True, test_missing_producer=False,
+                 wait_limit_s=0.0):
+        if not grids:
+            raise ValueError("empty batch")
+        dt = grids[0].dtype
+        if dt not in (torch.float32, torch.bfloat16) or any(g.dtype != dt for g in grids):
+            raise ValueError("batched grids are all float32 or all bfloat16")
+        self.A = list(grids)
+        self.B = [alloc_like(g) for g in grids]
+        geo = [grid_geom(g) for g in grids]
+        self.device = grids[0].device
+        flags = (0 if graph else _lib.JAC_BATCH_NO_GRAPH) | \
+            (_lib.JAC_BATCH_TEST_MISSING_PRODUCER if test_missing_producer else 0)
+        with torch.cuda.device(self.device):
+            self._h = _lib.jacobi_batch_create(
+                [g[:3] for g in geo], [g[3] for g in geo], [a.data_ptr() for a in self.A],
+                [b.data_ptr() for b in self.B], list(nsweeps), t, nchunk, _DT[dt],
+                _stream_ptr(self.device), flags, wait_limit_s)
+        self.count = len(grids)
+
+    def run(self):
+        with torch.cuda.device(self.device):
+            fb = _lib.jacobi_batch_run(self._h, self.count)
+        return [b if f else a for a, b, f in zip(self.A, self.B, fb)]
+
+    def info(self):
+        return _lib.jacobi_batch_info(self._h, self.count)
+
+    def check(self):
+        with torch.cuda.device(self.device):
+            _lib.jacobi_batch_check(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            with torch.cuda.device(self.device):
+                _lib.jacobi_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

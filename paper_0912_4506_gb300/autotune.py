@@ -1,0 +1,85 @@
+"""Autotuner for the temporal-blocking depth (and k-chunking) of batched grids.
+
+For every distinct grid shape it times the batched persistent kernel itself on
+enough replicas of that shape to fill the GPU, for each candidate depth, and
+keeps the fastest (lattice-site updates per second).  Results are cached in a
+JSON file keyed by device name, dtype and shape, so a batch is tuned once.
+The paper chose its blocking parameters experimentally as well (Sect. 1.4: the
+parameter space is large and the best values were found by measurement).
+"""
+import json
+import os
+import time
+
+import torch
+
+from . import api
+
+DEFAULT_CANDIDATES = (2, 3, 4, 5, 6)
+
+
+def cache_path():
+    base = os.environ.get("JACOBI_GB300_CACHE",
+                          os.path.join(os.path.expanduser("~"), ".cache", "paper_0912_4506_gb300"))
+    os.makedirs(base, exist_ok=True)
+    return os.path.join(base, "autotune.json")
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _key(dev, dtype, shape):
+    return f"{torch.cuda.get_device_name(dev)}|{dtype}|{shape[0]}x{shape[1]}x{shape[2]}"
+
+
+def _time_shape(shape, dtype, t, sweeps, device, reps):
+    nx, ny, nz = shape
+    grids = []
+    for _ in range(reps):
+        g = api.alloc_grid(nx, ny, nz, dtype, device)
+        g.uniform_()
+        grids.append(g)
+    b = api.Batch(grids, [sweeps] * reps, t=[t] * reps)
+    b.run()  # warm-up
+    torch.cuda.synchronize(device)
+    t0 = time.perf_counter()
+    b.run()
+    torch.cuda.synchronize(device)
+    dt = time.perf_counter() - t0
+    b.check()
+    b.close()
+    return reps * nx * ny * nz * sweeps / dt
+
+
+def tune(shapes, dtype="f32", candidates=DEFAULT_CANDIDATES, sweeps=24, device="cuda",
+         use_cache=True):
+    """Best depth per shape (list aligned with `shapes`) and the measurements."""
+    path = cache_path()
+    cache = _load(path) if use_cache else {}
+    dev = torch.device(device)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    out, table = [], {}
+    for shape in shapes:
+        key = _key(dev, dtype, shape)
+        if key in cache:
+            out.append(cache[key]["t"])
+            table[key] = cache[key]
+            continue
+        nx, ny, nz = shape
+        cells = nx * ny * nz
+        # replicas: enough tiles to cover every SM a few times, bounded memory
+        reps = max(1, min(64, (4 * sms * 64 * 32) // max(cells // 8, 1) + 1))
+        rates = {t: _time_shape(shape, dtype, t, sweeps, dev, reps) for t in candidates}
+        best = max(rates, key=rates.get)
+        cache[key] = {"t": best, "glups": {str(k): v / 1e9 for k, v in rates.items()}}
+        table[key] = cache[key]
+        out.append(best)
+    if use_cache:
+        with open(path, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+    return out, table

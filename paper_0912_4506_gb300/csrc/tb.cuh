@@ -27,17 +27,27 @@
 // the fixed Dirichlet boundary.  All arithmetic follows Eq. 1's operand order;
 // a pass of depth T therefore returns bit for bit what T plain sweeps return.
 //
+// The k-march is unrolled by 6, the period of the ring slot (NS = 6), of the
+// level buffers' parity (2) and of the register rotation (3), so every shared-
+// memory offset and register role is a compile-time constant.  Tiles whose
+// extended region lies inside the interior in x and y take a path without the
+// per-cell boundary selects.
+//
 // Modes: MODE_PLAIN (Eq. 1), MODE_RHS (the refinement's correction sweep, adds
 // rho before the product), MODE_ADJ (the adjoint sweep on a zero boundary, and
 // accumulation of RN(1/6)*lambda at the face-neighbouring interior cells into
 // the boundary gradient).
 #pragma once
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace jac {
 
 enum { MODE_PLAIN = 0, MODE_RHS = 1, MODE_ADJ = 2 };
+
+constexpr int kRing = 6;  // TMA ring slots (the unroll period)
 
 struct TBArgs {
     Geom g;
@@ -62,51 +72,67 @@ struct TBLayout {
     }
 };
 
-template <class Tr, int V, int NW, int T, int MODE, int NS>
-__global__ void __launch_bounds__(NW * 32, 1)
-    tb_sweep_kernel(const __grid_constant__ CUtensorMap tmap, const TBArgs a) {
+template <int N>
+using IC = std::integral_constant<int, N>;
+
+// One output tile of one temporally-blocked pass.  `smem` is the CTA's dynamic
+// shared memory (TBLayout), `s_abort` a shared flag.  Returns false when a TMA
+// wait timed out (status already recorded).  All threads of the CTA call it.
+template <class Tr, int V, int NW, int T, int MODE, bool FAST>
+__device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a, int bx,
+                                        int by, int bz, unsigned char* smem, int* s_abort) {
     using S = typename Tr::S;
     using C = typename Tr::C;
+    constexpr int NS = kRing;
     using L = TBLayout<V, NW, T, NS, S>;
     constexpr int EX = L::EX, EY = L::EY, PLANE = L::PLANE;
     constexpr uint32_t kPlaneBytes = PLANE * sizeof(S);
-    extern __shared__ __align__(1024) unsigned char smem[];
+    constexpr int OY = EY - 2 * T;
+    static_assert(OY >= 1, "tile too small for the depth");
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     S* ring = reinterpret_cast<S*>(smem + L::HEADER);
     S* lvl = ring + NS * PLANE;
-    __shared__ int s_abort;
 
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-    const Geom g = a.g;
-    constexpr int OY = EY - 2 * T;
-    const int X0 = a.x0_first + (int)blockIdx.x * a.ox;
-    const int Y0 = 1 - T + (int)blockIdx.y * OY;
+    const Geom& g = a.g;
+    const int X0 = a.x0_first + bx * a.ox;
+    const int Y0 = 1 - T + by * OY;
     const int ox0 = X0 + T, oy0 = Y0 + T;
-    const int kz0 = 1 + (int)blockIdx.z * a.kz;
+    const int kz0 = 1 + bz * a.kz;
     const int kz1 = min(g.nz + 1, kz0 + a.kz);
     const int Zlo = kz0 - T;
     const int M = (kz1 - kz0) + 2 * T;
     const int gy = Y0 + w;
     const int gx0 = X0 + lane * V;
+    const int smax = min(w, EY - 1 - w);  // deepest level this warp's row takes part in
 
     bool inxy[V], outxy[V];
     bool all_out = true, all_in = true;
 #pragma unroll
     for (int e = 0; e < V; ++e) {
         const int x = gx0 + e;
-        inxy[e] = (x >= 1) && (x <= g.nx) && (gy >= 1) && (gy <= g.ny);
-        outxy[e] = inxy[e] && (x >= ox0) && (x < ox0 + a.ox) && (gy >= oy0) && (gy < oy0 + OY);
+        inxy[e] = FAST || ((x >= 1) && (x <= g.nx) && (gy >= 1) && (gy <= g.ny));
+        outxy[e] = inxy[e] && (x >= ox0) && (x < ox0 + a.ox) && (x <= g.nx) && (gy >= oy0) &&
+                   (gy < oy0 + OY) && (gy <= g.ny) && (x >= 1) && (gy >= 1);
         all_out = all_out && outxy[e];
         all_in = all_in && inxy[e];
     }
+    // boundary-gradient faces touched by this thread's cells (MODE_ADJ)
+    bool face_xy = false;
+    if (MODE == MODE_ADJ) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const int x = gx0 + e;
+            face_xy = face_xy ||
+                      (outxy[e] && (x == 1 || x == g.nx || gy == 1 || gy == g.ny));
+        }
+    }
 
     if (tid == 0) {
-        s_abort = 0;
 #pragma unroll 1
         for (int i = 0; i < NS; ++i) mbar_init(&bars[i], 1);
         fence_mbar_init();
-        prefetch_tmap(&tmap);
     }
     __syncthreads();
     int issued = 0;  // planes issued so far (thread 0 only)
@@ -114,13 +140,13 @@ __global__ void __launch_bounds__(NW * 32, 1)
 #pragma unroll 1
         for (int i = 0; i < NS && i < M; ++i) {
             mbar_arrive_expect_tx(&bars[i], kPlaneBytes);
-            tma_load_3d(ring + i * PLANE, &tmap, &bars[i], X0, Y0, Zlo + i);
+            tma_load_3d(ring + i * PLANE, tmap, &bars[i], X0, Y0, Zlo + i);
         }
         issued = min(NS, M);
     }
 
-    C r[T][3][V];  // per level s < T: planes (old, cur, new) of level s, own cells
-    C rq[(MODE == MODE_RHS) ? T + 1 : 1][V];  // rho FIFO: rq[j] = rho at plane Zlo+m-j
+    C r[T][3][V];                                 // per level s < T: 3 planes of level s
+    C rq[(MODE == MODE_RHS) ? T + 1 : 1][V];      // rho FIFO: rq[j] = rho at plane Zlo+m-j
 #pragma unroll
     for (int s = 0; s < T; ++s)
 #pragma unroll
@@ -137,111 +163,105 @@ __global__ void __launch_bounds__(NW * 32, 1)
     S* dst = static_cast<S*>(a.dst);
     S* grad = static_cast<S*>(a.grad);
     const long long rowoff = (long long)gy * g.px + gx0;  // valid only when used
+    const int mycol = w * EX + lane * V;
 
-    // boundary-gradient accumulation of one level's plane p (MODE_ADJ)
     auto adj_acc = [&](const C (&v)[V], int p) {
         if (p < kz0 || p >= kz1) return;
+        const bool zf = (p == 1) || (p == g.nz);
+        if (!face_xy && !zf) return;
 #pragma unroll
         for (int e = 0; e < V; ++e) {
             if (!outxy[e]) continue;
             const int x = gx0 + e;
             const C cv = Tr::mul(c6, v[e]);
-            if (x == 1) {
-                const long long o = g.lin(0, gy, p);
-                grad[o] = Tr::st(Tr::add(Tr::ld(grad[o]), cv));
-            }
-            if (x == g.nx) {
-                const long long o = g.lin(g.nx + 1, gy, p);
-                grad[o] = Tr::st(Tr::add(Tr::ld(grad[o]), cv));
-            }
-            if (gy == 1) {
-                const long long o = g.lin(x, 0, p);
-                grad[o] = Tr::st(Tr::add(Tr::ld(grad[o]), cv));
-            }
-            if (gy == g.ny) {
-                const long long o = g.lin(x, g.ny + 1, p);
-                grad[o] = Tr::st(Tr::add(Tr::ld(grad[o]), cv));
-            }
-            if (p == 1) {
-                const long long o = g.lin(x, gy, 0);
-                grad[o] = Tr::st(Tr::add(Tr::ld(grad[o]), cv));
-            }
-            if (p == g.nz) {
-                const long long o = g.lin(x, gy, g.nz + 1);
-                grad[o] = Tr::st(Tr::add(Tr::ld(grad[o]), cv));
-            }
+            auto acc = [&](long long o) { grad[o] = Tr::st(Tr::add(Tr::ld(grad[o]), cv)); };
+            if (x == 1) acc(g.lin(0, gy, p));
+            if (x == g.nx) acc(g.lin(g.nx + 1, gy, p));
+            if (gy == 1) acc(g.lin(x, 0, p));
+            if (gy == g.ny) acc(g.lin(x, g.ny + 1, p));
+            if (p == 1) acc(g.lin(x, gy, 0));
+            if (p == g.nz) acc(g.lin(x, gy, g.nz + 1));
         }
     };
 
-    int m = 0;
-#pragma unroll 1
-    for (; m < M; ++m) {
-        const int slot = m % NS;
-        if (!mbar_wait_bounded(&bars[slot], (uint32_t)((m / NS) & 1))) {
+    int cur_m = 0;  // step being executed (for the clean-up after a timeout)
+    // One step of the k-march; PH = m mod 6 fixes slot, parity and rotation.
+    auto step = [&](auto ph, int m) -> bool {
+        constexpr int PH = decltype(ph)::value;
+        cur_m = m;
+        constexpr int SLOT = PH % NS;
+        constexpr int PSLOT = (PH + NS - 1) % NS;  // slot of plane Zlo+m-1
+        constexpr int PAR = PH & 1;
+        constexpr int OLD = PH % 3, CUR = (PH + 1) % 3, NEW = (PH + 2) % 3;
+        if (!mbar_wait_bounded(&bars[SLOT], (uint32_t)((m / NS) & 1))) {
             atomicOr(a.status, kStatusTimeout);
-            s_abort = 1;
+            *s_abort = 1;
         }
         // ---- level 0: plane Zlo + m, own cells
+        const int p0 = Zlo + m;
         {
-            const int p = Zlo + m;
-            const bool zin = (p >= 1) && (p <= g.nz);
-            const Vec<S, V> t =
-                *reinterpret_cast<const Vec<S, V>*>(ring + slot * PLANE + w * EX + lane * V);
+            const Vec<S, V> t = *reinterpret_cast<const Vec<S, V>*>(ring + SLOT * PLANE + mycol);
 #pragma unroll
-            for (int e = 0; e < V; ++e) r[0][2][e] = Tr::ld(t.v[e]);
+            for (int e = 0; e < V; ++e) r[0][NEW][e] = Tr::ld(t.v[e]);
             if (MODE == MODE_RHS) {
+                const bool zin0 = (p0 >= 1) && (p0 <= g.nz);
 #pragma unroll
                 for (int j = ((MODE == MODE_RHS) ? T : 0); j >= 1; --j)
 #pragma unroll
                     for (int e = 0; e < V; ++e) rq[j][e] = rq[j - 1][e];
-                if (zin && all_in) {
-                    const Vec<S, V> q = ldg_vec<S, V>(rho + g.plane * p + rowoff);
+                if (zin0 && all_in) {
+                    const Vec<S, V> q = ldg_vec<S, V>(rho + g.plane * p0 + rowoff);
 #pragma unroll
                     for (int e = 0; e < V; ++e) rq[0][e] = Tr::ld(q.v[e]);
                 } else {
 #pragma unroll
                     for (int e = 0; e < V; ++e)
-                        rq[0][e] = (zin && inxy[e]) ? Tr::ld(rho[g.plane * p + rowoff + e]) : C(0);
+                        rq[0][e] = (zin0 && inxy[e]) ? Tr::ld(rho[g.plane * p0 + rowoff + e])
+                                                     : C(0);
                 }
             }
-            if (MODE == MODE_ADJ && T > 0) adj_acc(r[0][2], p);
+            if (MODE == MODE_ADJ) adj_acc(r[0][NEW], p0);
         }
         // ---- levels 1..T
 #pragma unroll
         for (int s = 1; s <= T; ++s) {
-            if (m < s) continue;                        // pipeline fill
-            if (w < s || w >= EY - s) continue;         // row outside level s's region
-            const int q = Zlo + m - s;
+            if (m < s) continue;     // pipeline fill
+            if (s > smax) continue;  // row outside level s's region
+            const int q = p0 - s;
             const bool zin = (q >= 1) && (q <= g.nz);
-            const S* nb = (s == 1) ? ring + ((m - 1) % NS) * PLANE
-                                   : lvl + ((s - 2) * 2 + ((m - 1) & 1)) * PLANE;
-            const Vec<S, V> vn = *reinterpret_cast<const Vec<S, V>*>(nb + (w - 1) * EX + lane * V);
-            const Vec<S, V> vs = *reinterpret_cast<const Vec<S, V>*>(nb + (w + 1) * EX + lane * V);
-            const C left = __shfl_up_sync(FULL, r[s - 1][1][V - 1], 1);
-            const C right = __shfl_down_sync(FULL, r[s - 1][1][0], 1);
+            const S* nb = (s == 1) ? ring + PSLOT * PLANE
+                                   : lvl + ((s - 2) * 2 + (PAR ^ 1)) * PLANE;
+            const Vec<S, V> vn = *reinterpret_cast<const Vec<S, V>*>(nb + mycol - EX);
+            const Vec<S, V> vs = *reinterpret_cast<const Vec<S, V>*>(nb + mycol + EX);
+            const C left = __shfl_up_sync(FULL, r[s - 1][CUR][V - 1], 1);
+            const C right = __shfl_down_sync(FULL, r[s - 1][CUR][0], 1);
             C out[V];
+            if (zin) {
 #pragma unroll
-            for (int e = 0; e < V; ++e) {
-                const C l = (e == 0) ? left : r[s - 1][1][e - 1];
-                const C rr = (e == V - 1) ? right : r[s - 1][1][e + 1];
-                C sum = Tr::add(l, rr);
-                sum = Tr::add(sum, Tr::ld(vn.v[e]));
-                sum = Tr::add(sum, Tr::ld(vs.v[e]));
-                sum = Tr::add(sum, r[s - 1][0][e]);
-                sum = Tr::add(sum, r[s - 1][2][e]);
-                if (MODE == MODE_RHS) sum = Tr::add(sum, rq[s][e]);
-                const C val = Tr::rnd(Tr::mul(sum, c6));
-                out[e] = (inxy[e] && zin) ? val : r[s - 1][1][e];
+                for (int e = 0; e < V; ++e) {
+                    const C l = (e == 0) ? left : r[s - 1][CUR][e - 1];
+                    const C rr = (e == V - 1) ? right : r[s - 1][CUR][e + 1];
+                    C sum = Tr::add(l, rr);
+                    sum = Tr::add(sum, Tr::ld(vn.v[e]));
+                    sum = Tr::add(sum, Tr::ld(vs.v[e]));
+                    sum = Tr::add(sum, r[s - 1][OLD][e]);
+                    sum = Tr::add(sum, r[s - 1][NEW][e]);
+                    if (MODE == MODE_RHS) sum = Tr::add(sum, rq[s][e]);
+                    const C val = Tr::rnd(Tr::mul(sum, c6));
+                    out[e] = (FAST || inxy[e]) ? val : r[s - 1][CUR][e];
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) out[e] = r[s - 1][CUR][e];
             }
             if (s < T) {
                 Vec<S, V> o;
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
-                    r[s < T ? s : 0][2][e] = out[e];
+                    r[s < T ? s : 0][NEW][e] = out[e];
                     o.v[e] = Tr::st(out[e]);
                 }
-                *reinterpret_cast<Vec<S, V>*>(lvl + ((s - 1) * 2 + (m & 1)) * PLANE + w * EX +
-                                              lane * V) = o;
+                *reinterpret_cast<Vec<S, V>*>(lvl + ((s - 1) * 2 + PAR) * PLANE + mycol) = o;
                 if (MODE == MODE_ADJ) adj_acc(out, q);
             } else if (q >= kz0 && q < kz1) {
                 const long long o = g.plane * q + rowoff;
@@ -257,32 +277,75 @@ __global__ void __launch_bounds__(NW * 32, 1)
                 }
             }
         }
-        // ---- rotate the per-level k window
-#pragma unroll
-        for (int s = 0; s < T; ++s)
-#pragma unroll
-            for (int e = 0; e < V; ++e) {
-                r[s][0][e] = r[s][1][e];
-                r[s][1][e] = r[s][2][e];
-            }
         __syncthreads();
-        if (s_abort) break;
+        if (*s_abort) return false;
         // the slot of plane Zlo+m-1 is free now: refill it with plane Zlo+m-1+NS
         if (tid == 0 && m >= 1 && issued < M) {
-            const int sl = (m - 1) % NS;
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bars[sl], kPlaneBytes);
-            tma_load_3d(ring + sl * PLANE, &tmap, &bars[sl], X0, Y0, Zlo + issued);
+            mbar_arrive_expect_tx(&bars[PSLOT], kPlaneBytes);
+            tma_load_3d(ring + PSLOT * PLANE, tmap, &bars[PSLOT], X0, Y0, Zlo + issued);
             ++issued;
         }
-    }
-    if (m < M && tid == 0) {
-        // timed out: let the copies already in flight land before the CTA's shared
-        // memory is released (each wait bounded again)
+        return true;
+    };
+
+    int m = 0;
+    bool ok = true;
 #pragma unroll 1
-        for (int p = m + 1; p < issued; ++p)
+    for (; m + 6 <= M; m += 6) {
+        if (!step(IC<0>{}, m) || !step(IC<1>{}, m + 1) || !step(IC<2>{}, m + 2) ||
+            !step(IC<3>{}, m + 3) || !step(IC<4>{}, m + 4) || !step(IC<5>{}, m + 5)) {
+            ok = false;
+            break;
+        }
+    }
+    if (ok) {
+        // remainder (M mod 6 steps), same phases
+        const int left = M - m;
+        if (left > 0) ok = step(IC<0>{}, m);
+        if (ok && left > 1) ok = step(IC<1>{}, m + 1);
+        if (ok && left > 2) ok = step(IC<2>{}, m + 2);
+        if (ok && left > 3) ok = step(IC<3>{}, m + 3);
+        if (ok && left > 4) ok = step(IC<4>{}, m + 4);
+    }
+    if (!ok && tid == 0) {
+        // timed out: let the copies still in flight (planes cur_m .. issued-1) land
+        // before the shared memory is reused or released (each wait bounded again)
+#pragma unroll 1
+        for (int p = cur_m; p < issued; ++p)
             (void)mbar_wait_bounded(&bars[p % NS], (uint32_t)((p / NS) & 1), 500000000ull);
     }
+    __syncthreads();
+    if (ok && tid == 0) {
+#pragma unroll 1
+        for (int i = 0; i < NS; ++i) mbar_inval(&bars[i]);
+    }
+    return ok;
+}
+
+// CTA-uniform test: the extended tile lies inside the interior in x and y.
+template <int V, int NW, int T>
+__device__ __forceinline__ bool tile_inside_xy(const TBArgs& a, int bx, int by) {
+    const int X0 = a.x0_first + bx * a.ox;
+    const int Y0 = 1 - T + by * (NW - 2 * T);
+    return X0 >= 1 && X0 + 32 * V - 1 <= a.g.nx && Y0 >= 1 && Y0 + NW - 1 <= a.g.ny;
+}
+
+template <class Tr, int V, int NW, int T, int MODE, int NS>
+__global__ void __launch_bounds__(NW * 32, 1)
+    tb_sweep_kernel(const __grid_constant__ CUtensorMap tmap, const TBArgs a) {
+    static_assert(NS == kRing, "the k-march is unrolled by the ring size");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ int s_abort;
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        prefetch_tmap(&tmap);
+    }
+    const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
+    if (tile_inside_xy<V, NW, T>(a, bx, by))
+        tb_tile<Tr, V, NW, T, MODE, true>(&tmap, a, bx, by, bz, smem, &s_abort);
+    else
+        tb_tile<Tr, V, NW, T, MODE, false>(&tmap, a, bx, by, bz, smem, &s_abort);
 }
 
 }  // namespace jac

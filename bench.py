@@ -217,6 +217,156 @@ def variant_rows(dev, steps):
     return rows
 
 
+def variant_precision(dev, n=1024, outer=20, inner=50, t=4):
+    """Laplace problem on an n^3 interior: FP64 reference = outer*inner plain FP64
+    sweeps; FP32 and bf16 refinement (inner sweeps in low precision, FP64
+    residual).  GLUP/s counts outer*inner sweeps over the total time including the
+    residual steps; error = max |u_refined - u_fp64| over the grid."""
+    import torch
+    from paper_0912_4506_gb300 import api, inputs
+    total = outer * inner
+    u0 = inputs.laplace_boundary_torch(n, n, n, device=dev)
+    g0 = api.as_grid(u0, n)
+    rows = {}
+    j = api.Jacobi(g0)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    ref = j.sweep(total, 1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    rows["fp64_plain"] = {"glups": round(n ** 3 * total / ms / 1e6, 2), "ms": round(ms, 1),
+                          "sweeps": total}
+    ref_keep = ref
+    u_init = inputs.laplace_boundary_torch(n, n, n, device=dev)
+    for dtype in ("f32", "bf16"):
+        r = api.Refiner(api.as_grid(u_init, n), dtype)
+        r.run(1, 2, t)  # warm-up (plans, descriptors)
+        torch.cuda.synchronize()
+        e0.record()
+        out = r.run(outer, inner, t)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        err = float((out - ref_keep).abs().max())
+        scale = float(ref_keep.abs().max())
+        rows[f"{dtype}_refined"] = {
+            "glups": round(n ** 3 * total / ms / 1e6, 2), "ms": round(ms, 1),
+            "outer": outer, "inner": inner, "t": t, "max_abs_err_vs_fp64": err,
+            "max_rel_err_vs_fp64": err / scale}
+        r.close()
+        del r, out
+        torch.cuda.empty_cache()
+    j.close()
+    del j, ref, ref_keep, u0, g0, u_init
+    torch.cuda.empty_cache()
+    rows["config"] = {"n": n, "outer": outer, "inner": inner,
+                      "boundary": "u = x^2 - y^2 + 0.5 z (discrete-harmonic)"}
+    return rows
+
+
+def variant_batched(dev):
+    """64 FP32 grids (shapes multiples of 8 in [32,256], sweeps in [10,200], seed 2),
+    depth per grid from the autotuner, one persistent launch in a CUDA graph."""
+    import torch
+    from paper_0912_4506_gb300 import api, autotune, inputs
+    specs = inputs.batch_specs()
+    shapes = [s[:3] for s in specs]
+    ts, _ = autotune.tune(shapes, "f32")
+    grids = []
+    for i, (nx, ny, nz, n) in enumerate(specs):
+        a = inputs.to_dtype(inputs.uniform_grid_f64(nx, ny, nz, g=i), "f32",
+                            px=inputs.row_pitch(nx, "f32"))
+        grids.append(api.from_numpy(a, nx, dev))
+    b = api.Batch(grids, [s[3] for s in specs], t=ts)
+    b.run()
+    torch.cuda.synchronize()
+    reps = 3
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        b.run()
+    e1.record()
+    torch.cuda.synchronize()
+    b.check()
+    ms = e0.elapsed_time(e1) / reps
+    lups = sum(nx * ny * nz * n for nx, ny, nz, n in specs)
+    info = b.info()
+    hist = {}
+    for t in info["t"]:
+        hist[str(t)] = hist.get(str(t), 0) + 1
+    b.close()
+    return {"glups": round(lups / ms / 1e6, 2), "ms_per_run": round(ms, 3), "grids": len(specs),
+            "lups_per_run": lups, "work_items": info["items"], "persistent_ctas": info["ctas"],
+            "depth_histogram": hist, "launches_per_run": 1}
+
+
+def variant_adjoint(dev, n=256, nsweeps=50, t=4):
+    """256^3 FP32, 50 sweeps: forward (blocked), adjoint (blocked, with the boundary
+    gradient), beside the plain FP32 sweep; error of the FP32 gradient against the
+    FP64 adjoint of the same loss."""
+    import torch
+    from paper_0912_4506_gb300 import api, inputs
+    x = inputs.uniform_grid_f64(n, n, n)
+    W = inputs.normal_grid_f64(n, n, n)
+    rows = {}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize()
+        ev[0].record()
+        for _ in range(reps):
+            fn()
+        ev[1].record()
+        torch.cuda.synchronize()
+        return ev[0].elapsed_time(ev[1]) / reps
+
+    grads = {}
+    for dtype in ("f32", "f64"):
+        px = inputs.row_pitch(n, dtype)
+        xg = api.from_numpy(inputs.to_dtype(x, dtype, px=px), n, dev)
+        Wg = api.from_numpy(inputs.to_dtype(W, dtype, px=px), n, dev)
+        j = api.Jacobi(xg)
+        if dtype == "f32":
+            ms_plain = timed(lambda: j.sweep(nsweeps, 1))
+            ms_fwd = timed(lambda: j.sweep(nsweeps, t))
+        lam = api.alloc_like(Wg)
+        gb = api.alloc_like(Wg)
+        jl = api.Jacobi(lam)
+        # timing: repeated adjoint calls continue the iteration (same work per call)
+        ms_adj = timed(lambda: jl.adjoint(gb, nsweeps, t))
+        # the gradient itself: lambda_n = W on the interior, grad_g starts at W's
+        # boundary layer (the direct term)
+        lam.zero_()
+        lam[1:-1, 1:-1, 1:-1].copy_(Wg[1:-1, 1:-1, 1:-1])
+        gb.copy_(Wg)
+        gb[1:-1, 1:-1, 1:-1].zero_()
+        out = jl.adjoint(gb, nsweeps, t)
+        jl.check()
+        torch.cuda.synchronize()
+        g = gb.clone()
+        g[1:-1, 1:-1, 1:-1].copy_(out[1:-1, 1:-1, 1:-1])
+        grads[dtype] = g.double()
+        jl.close()
+        if dtype == "f32":
+            rows["plain_fwd_glups"] = round(n ** 3 * nsweeps / ms_plain / 1e6, 2)
+            rows["tb_fwd_glups"] = round(n ** 3 * nsweeps / ms_fwd / 1e6, 2)
+            rows["adjoint_glups"] = round(n ** 3 * nsweeps / ms_adj / 1e6, 2)
+        else:
+            rows["adjoint_fp64_glups"] = round(n ** 3 * nsweeps / ms_adj / 1e6, 2)
+        j.close()
+    err = float((grads["f32"] - grads["f64"]).abs().max())
+    rows["grad_max_abs_err_f32_vs_f64"] = err
+    rows["grad_max_rel_err_f32_vs_f64"] = err / float(grads["f64"].abs().max())
+    rows["config"] = {"n": n, "sweeps": nsweeps, "t": t, "loss": "sum(W * A_n), W ~ N(0,1) seed 3"}
+    torch.cuda.empty_cache()
+    return rows
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -338,6 +488,9 @@ def run_ours(args):
     torch.cuda.empty_cache()
     if world == 1 and not args.no_variants:
         line["variants"] = variant_rows(dev, max(2, min(args.steps, 3)))
+        line["precision_1024"] = variant_precision(dev)
+        line["batched_64"] = variant_batched(dev)
+        line["adjoint_256"] = variant_adjoint(dev)
     if world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(a64)
         line["cpu_baseline"] = {"value": round(rate, 4), "unit": "GLUP/s", "cores": cores,

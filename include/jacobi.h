@@ -82,6 +82,8 @@ typedef struct {
     int threads;           /* threads per CTA                                     */
     int smem_bytes;        /* dynamic shared memory per CTA                       */
     int grid_x, grid_y, grid_z;
+    int emu_adds;          /* FP64 plain sweep: additions done on the integer pipes
+                              when the grid's values allow it (see jacobi_emulated_add) */
 } jacobi_plan_info;
 
 /*
@@ -254,6 +256,18 @@ JAC_API int jacobi_batch_destroy(jacobi_batch_t b);
 JAC_API int jacobi_sweep_noalloc(int nx, int ny, int nz, int dtype, void *grid,
                                  long long row_pitch, int nsweeps, int t, void *stream,
                                  int sync);
+
+/*
+ * jacobi_emulated_add — out[i] = a[i] + b[i] computed the way the FP64 plain
+ * sweep computes its integer-pipe additions: exact IEEE-754 binary64 addition
+ * with round-to-nearest-even, done with integer instructions for positive
+ * normal operands whose exponents differ by at most 31 (the FP64 unit for every
+ * other pair).  The results equal the FP64 unit's bit for bit; this entry point
+ * lets tests check that on any set of pairs.  Device arrays of n doubles;
+ * asynchronous on `stream`.
+ */
+JAC_API int jacobi_emulated_add(const double *a, const double *b, double *out, long long n,
+                                void *stream);
 
 /* jacobi_check — wait for the handle's stream and report a device-side status
  * (JAC_ETIMEOUT when a bounded wait ran out) or a CUDA error (JAC_ECUDA).  The

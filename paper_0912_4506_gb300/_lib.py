@@ -17,7 +17,7 @@ EXPORTS = ["jacobi_create", "jacobi_sweep", "jacobi_sweep_ex", "jacobi_plan",
            "jacobi_upload", "jacobi_download", "jacobi_check", "jacobi_destroy",
            "jacobi_strerror", "jacobi_version", "jacobi_sweep_noalloc",
            "jacobi_batch_create", "jacobi_batch_run", "jacobi_batch_info", "jacobi_batch_check",
-           "jacobi_batch_destroy"]
+           "jacobi_batch_destroy", "jacobi_emulated_add"]
 
 JAC_BATCH_NO_GRAPH, JAC_BATCH_TEST_MISSING_PRODUCER = 1, 2
 
@@ -32,7 +32,7 @@ class JacobiError(RuntimeError):
 class PlanInfo(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int) for n in (
         "kernel", "t", "passes", "remainder_t", "tile_x", "tile_y", "ext_x", "ext_y",
-        "kchunk", "threads", "smem_bytes", "grid_x", "grid_y", "grid_z")]
+        "kchunk", "threads", "smem_bytes", "grid_x", "grid_y", "grid_z", "emu_adds")]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -73,6 +73,7 @@ def load(path=None):
         "jacobi_batch_info": ([P, PI, PI, PI, PI], I),
         "jacobi_batch_check": ([P], I),
         "jacobi_batch_destroy": ([P], I),
+        "jacobi_emulated_add": ([P, P, P, LL, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -204,3 +205,7 @@ def jacobi_batch_check(h):
 
 def jacobi_batch_destroy(h):
     _ck(load().jacobi_batch_destroy(h), "jacobi_batch_destroy")
+
+
+def jacobi_emulated_add(a_ptr, b_ptr, out_ptr, n, stream):
+    _ck(load().jacobi_emulated_add(a_ptr, b_ptr, out_ptr, n, stream), "jacobi_emulated_add")

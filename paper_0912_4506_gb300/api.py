@@ -206,6 +206,7 @@ class Refiner:
     def __init__(self, u0, dtype="f32"):
         nx, ny, nz, _ = grid_geom(u0)
         dt = torch_dtype(dtype)
+        self.u0 = u0
         self.u = [alloc_like(u0), alloc_like(u0)]
         self.u[0].copy_(u0)
         self.u[1].copy_(u0)
@@ -215,7 +216,10 @@ class Refiner:
         self.solver = Jacobi(self.e0, self.e1)
 
     def run(self, outer, inner, t=0):
+        """Refine from u0 (every call starts again from u0); returns the grid that
+        holds the result."""
         u, e0, rho = self.u, self.e0, self.rho
+        u[0].copy_(self.u0)
         e_cur = e0
         cur = 0
         for _ in range(outer):

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -16,6 +17,10 @@
 
 using namespace jac;
 
+namespace {
+constexpr int kDefaultF64Emu = 2;
+}
+
 struct jacobi_s {
     int dtype;
     Geom g;
@@ -24,7 +29,7 @@ struct jacobi_s {
     cudaStream_t stream;
     int device;
     int num_sms;
-    int* status;          // device status word (owned)
+    int* status;          // device status word (owned); status[16]: FP64 range flag
     CUtensorMap map_a;    // TMA descriptors of A and B (box set per entry shape)
     CUtensorMap map_b;
     int map_box_x, map_box_y;
@@ -109,9 +114,31 @@ void ensure_attrs(const std::vector<TBEntry>& tab, int device) {
     }
 }
 
+// Number of the five additions the FP64 plain sweep does on the integer pipes
+// (when the range check allows it); JACOBI_F64_EMU overrides (0..5).
+int f64_emu_count() {
+    static int n = -1;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        n = kDefaultF64Emu;
+        if (const char* e = getenv("JACOBI_F64_EMU")) {
+            const int v = atoi(e);
+            if (v >= 0 && v <= 5) n = v;
+        }
+    });
+    return n;
+}
+
 const PlainEntry* plain_for(int dtype) {
-    return dtype == JAC_F64 ? plain_entry_f64() : dtype == JAC_F32 ? plain_entry_f32()
-                                                                   : plain_entry_bf16();
+    if (dtype == JAC_F64) {
+        int n = 0;
+        const PlainEntry* tab = plain_entries_f64(&n);
+        const int want = f64_emu_count();
+        for (int i = 0; i < n; ++i)
+            if (tab[i].nemu == want) return &tab[i];
+        return plain_entry_f64();
+    }
+    return dtype == JAC_F32 ? plain_entry_f32() : plain_entry_bf16();
 }
 
 // Geometry of one temporally-blocked pass for an entry.
@@ -236,6 +263,7 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         if (info_only) {
             std::memset(info_only, 0, sizeof(*info_only));
             info_only->kernel = JAC_KERNEL_PLAIN;
+            info_only->emu_adds = pe->nemu;
             info_only->t = 1;
             info_only->passes = nsweeps;
             info_only->tile_x = 32 * pe->V;
@@ -249,10 +277,18 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
             info_only->grid_z = grid.z;
             return JAC_OK;
         }
+        const int* fast = nullptr;
+        if (pe->nemu > 0 && nsweeps > 0) {
+            // the integer-pipe additions need every value positive and normal
+            fast = h->status + 16;
+            if (launch_range_check(static_cast<const double*>(h->a), h->g, h->status + 16,
+                                   h->stream) != cudaSuccess)
+                return JAC_ECUDA;
+        }
         for (int s = 0; s < nsweeps; ++s) {
             const void* src = (s & 1) ? h->b : h->a;
             void* dst = (s & 1) ? h->a : h->b;
-            if (pe->launch(src, dst, h->g, kchunk, grid, h->stream) != cudaSuccess)
+            if (pe->launch(src, dst, h->g, kchunk, grid, fast, h->stream) != cudaSuccess)
                 return JAC_ECUDA;
         }
         if (final_is_b) *final_is_b = nsweeps & 1;
@@ -347,11 +383,11 @@ int jacobi_create(jacobi_t* out, int nx, int ny, int nz, int dtype, void* grid_a
         delete h;
         return JAC_ECUDA;
     }
-    if (cudaMalloc(&h->status, sizeof(int)) != cudaSuccess) {
+    if (cudaMalloc(&h->status, 32 * sizeof(int)) != cudaSuccess) {
         delete h;
         return JAC_ENOMEM;
     }
-    if (cudaMemsetAsync(h->status, 0, sizeof(int), h->stream) != cudaSuccess ||
+    if (cudaMemsetAsync(h->status, 0, 32 * sizeof(int), h->stream) != cudaSuccess ||
         launch_boundary_copy(dtype, grid_a, grid_b, h->g, h->stream) != cudaSuccess) {
         cudaFree(h->status);
         delete h;

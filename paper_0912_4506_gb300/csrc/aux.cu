@@ -1,5 +1,9 @@
 // Auxiliary kernels: boundary-layer copy and the FP64 residual step of the
 // mixed-precision iterative refinement.
+#include <algorithm>
+
+#include "../../include/jacobi.h"
+#include "emu.cuh"
 #include "launch.h"
 
 namespace jac {
@@ -56,6 +60,46 @@ cudaError_t launch_boundary_copy(int dtype, const void* A, void* B, const Geom& 
             break;
     }
     return cudaGetLastError();
+}
+
+// Validity test for the integer-pipe additions of the FP64 plain sweep: every
+// cell of the padded grid (boundary layer included, row padding excluded) lies
+// in [2^-1000, 2^1000].  *flag must be 1 on entry; any cell outside clears it.
+__global__ void range_check_kernel(const double* __restrict__ A, const Geom g, int* flag) {
+    const long long nxp = g.nx + 2, rows = (long long)(g.ny + 2) * (g.nz + 2);
+    const unsigned long long lo = 0x0170000000000000ull;  // 2^-1000
+    const unsigned long long hi = 0x7E70000000000000ull;  // 2^1000
+    bool ok = true;
+    for (long long r = blockIdx.x; r < rows; r += gridDim.x) {
+        const double* row = A + r * g.px;
+        for (long long i = threadIdx.x; i < nxp; i += blockDim.x) {
+            const unsigned long long v = (unsigned long long)__double_as_longlong(__ldg(row + i));
+            ok = ok && v >= lo && v <= hi;
+        }
+    }
+    if (!__syncthreads_and(ok) && threadIdx.x == 0) *flag = 0;
+}
+
+cudaError_t launch_range_check(const double* A, const Geom& g, int* flag, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(flag, 0xFF, sizeof(int), st);  // nonzero = valid
+    if (e != cudaSuccess) return e;
+    range_check_kernel<<<1024, 256, 0, st>>>(A, g, flag);
+    return cudaGetLastError();
+}
+
+// Elementwise emulated addition (verification entry point of add_pos_exact).
+__global__ void emulated_add_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                    double* __restrict__ out, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double x = a[i], y = b[i];
+        const unsigned long long X = (unsigned long long)__double_as_longlong(x);
+        const unsigned long long Y = (unsigned long long)__double_as_longlong(y);
+        // positive normal operands with a finite sum take the integer path
+        const bool ok = (X >> 52) >= 1 && (X >> 52) <= 2045 && (Y >> 52) >= 1 &&
+                        (Y >> 52) <= 2045;
+        out[i] = ok ? add_pos_exact(x, y) : __dadd_rn(x, y);
+    }
 }
 
 // Residual step of the refinement, fused and streaming in k.  For every interior
@@ -137,3 +181,13 @@ cudaError_t launch_residual(const double* u_in, double* u_out, const Geom& gu, c
 }
 
 }  // namespace jac
+
+extern "C" int jacobi_emulated_add(const double* a, const double* b, double* out, long long n,
+                                   void* stream) {
+    if (n < 0 || (n > 0 && (!a || !b || !out))) return JAC_EINVAL;
+    if (n == 0) return JAC_OK;
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    jac::emulated_add_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        a, b, out, n);
+    return cudaGetLastError() == cudaSuccess ? JAC_OK : JAC_ECUDA;
+}

@@ -1,0 +1,67 @@
+// Exact IEEE-754 binary64 addition (round to nearest, ties to even) on the
+// integer pipes, for positive normal operands.
+//
+// GB300 executes FP64 at 2 operations per clock per SM; the plain FP64 sweep
+// (6 operations per lattice-site update) is therefore bound by the FP64 pipe
+// while the integer pipes and most issue slots idle.  Doing some of the five
+// additions of Eq. 1 with integer instructions lets both pipes work.  The result
+// is the correctly rounded sum, identical bit for bit to the FP64 unit's, so
+// the sweep stays bit-exact whichever additions are emulated.
+//
+// Method (written from the definition of binary64 and of rounding to nearest
+// even): take the operand X with the larger exponent and the other, Y (for
+// positive doubles the bit patterns order like the values), align Y's 53-bit significand to X's
+// exponent keeping 9 extra low bits plus a sticky bit for everything shifted
+// out, add, and round the 54- or 55-bit sum back to 53 bits with the usual
+// "add half-minus-one plus the kept LSB, then shift" step; the exponent follows
+// from the carry.  Exponent differences above 31 (the smaller operand then
+// only affects the sticky bit, and such lanes are rare) go to the FP64 unit.
+// Operands must be positive normal numbers whose sum stays finite; the caller
+// guarantees that (see range_check_kernel).
+#pragma once
+
+#include <stdint.h>
+
+namespace jac {
+
+__device__ __forceinline__ uint32_t shl32(uint32_t x, uint32_t n) {  // n in [0, 32]
+    uint32_t r;
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(x), "r"(n));
+    return r;
+}
+
+// The FP64-unit addition for the rare pairs the integer path leaves out.  It is
+// an out-of-line call so that warps with no such lane jump over it: an inlined
+// addition would be issued predicated-off and still hold the FP64 pipe, whose
+// time is exactly what the integer path is meant to save.
+static __device__ __noinline__ double add_fp64_unit(double a, double b) { return __dadd_rn(a, b); }
+
+__device__ __forceinline__ double add_pos_exact(double a, double b) {
+    const unsigned long long A = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long B = (unsigned long long)__double_as_longlong(b);
+    // order by the high words: when the exponents differ they decide, when they
+    // are equal either order works (no alignment shift)
+    const bool swap = (uint32_t)(A >> 32) < (uint32_t)(B >> 32);
+    const unsigned long long X = swap ? B : A;
+    const unsigned long long Y = swap ? A : B;
+    const uint32_t ex = (uint32_t)(X >> 52);
+    const uint32_t d = ex - (uint32_t)(Y >> 52);
+    const uint32_t dd = d > 31u ? 31u : d;  // keeps the integer path defined
+    const unsigned long long kMant = 0x000FFFFFFFFFFFFFull, kHidden = 0x0010000000000000ull;
+    const unsigned long long mx = ((X & kMant) | kHidden) << 9;
+    const unsigned long long my = ((Y & kMant) | kHidden) << 9;
+    // bits of my shifted out by dd (only its low word can lose bits, dd <= 31)
+    const uint32_t sticky = shl32((uint32_t)my, 32u - dd) != 0u ? 1u : 0u;
+    const unsigned long long S = mx + ((my >> dd) | sticky);  // in [2^61, 2^63)
+    const uint32_t c = (uint32_t)(S >> 62);                    // carry out of the add
+    const uint32_t sh = 9u + c;
+    const unsigned long long lsb = (S >> sh) & 1ull;
+    const unsigned long long R = (S + (((unsigned long long)0x100u << c) - 1ull) + lsb) >> sh;
+    double r = __longlong_as_double((long long)((((unsigned long long)(ex + c - 1u)) << 52) + R));
+    if (__any_sync(__activemask(), d > 31u)) {
+        if (d > 31u) r = add_fp64_unit(a, b);
+    }
+    return r;
+}
+
+}  // namespace jac

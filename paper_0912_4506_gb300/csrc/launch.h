@@ -29,12 +29,13 @@ struct TBEntry {
 };
 
 using PlainLaunchFn = cudaError_t (*)(const void* A, void* B, const Geom& g, int kchunk,
-                                      dim3 grid, cudaStream_t st);
+                                      dim3 grid, const int* fast, cudaStream_t st);
 
 struct PlainEntry {
     int dtype;
-    int V;    // cells per lane
-    int WY;   // warps (rows) per CTA
+    int V;     // cells per lane
+    int WY;    // warps (rows) per CTA
+    int nemu;  // additions done on the integer pipes when `fast` is set (FP64)
     PlainLaunchFn launch;
     const void* kernel;
 };
@@ -47,12 +48,14 @@ const TBEntry* tb_entries_f32_adj(int* n);
 const TBEntry* tb_entries_bf16(int* n);
 const TBEntry* tb_entries_bf16_rhs(int* n);
 const PlainEntry* plain_entry_f64();
+const PlainEntry* plain_entries_f64(int* n);  // all emulation variants
 const PlainEntry* plain_entry_f32();
 const PlainEntry* plain_entry_bf16();
 
 // Auxiliary kernels (aux.cu).
 cudaError_t launch_boundary_copy(int dtype, const void* A, void* B, const Geom& g,
                                  cudaStream_t st);
+cudaError_t launch_range_check(const double* A, const Geom& g, int* flag, cudaStream_t st);
 cudaError_t launch_residual(const double* u_in, double* u_out, const Geom& gu,
                             const void* e, void* rho, int lo_dtype, const Geom& glo,
                             cudaStream_t st);

@@ -179,7 +179,7 @@ extern "C" int jacobi_sweep_noalloc(int nx, int ny, int nz, int dtype, void* gri
         for (int s = 0; s < nsweeps; ++s) {
             const void* src = cur_other ? other : grid;
             void* dst = cur_other ? grid : other;
-            if (pe->launch(src, dst, g, kchunk, grid3, st) != cudaSuccess) return JAC_ECUDA;
+            if (pe->launch(src, dst, g, kchunk, grid3, nullptr, st) != cudaSuccess) return JAC_ECUDA;
             cur_other ^= 1;
         }
     } else {

@@ -11,6 +11,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "emu.cuh"
 
 namespace jac {
 
@@ -28,37 +29,25 @@ __device__ __forceinline__ void load_vec(const typename Tr::S* __restrict__ p, b
     }
 }
 
-template <class Tr, int V, int WY>
-__global__ void __launch_bounds__(32 * WY)
-    plain_sweep_kernel(const typename Tr::S* __restrict__ A, typename Tr::S* __restrict__ B,
-                       const Geom g, const int kchunk) {
+// The sweep of one chunk, with the first NEMU of the five additions done by
+// add_pos_exact (FP64 only; NEMU = 0: all on the FP64 unit).
+template <class Tr, int V, int NEMU>
+__device__ __forceinline__ void plain_march(const typename Tr::S* __restrict__ A,
+                                            typename Tr::S* __restrict__ B, const Geom& g,
+                                            int k0, int k1, int x0, int y, int lane,
+                                            bool loadable, const bool (&interior)[V],
+                                            bool all_interior, bool left_ok, bool right_ok,
+                                            long long row) {
     using S = typename Tr::S;
     using C = typename Tr::C;
-    constexpr int XOFF = (V == 1) ? 1 : 0;
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x;
-    const int x0 = XOFF + (int)(blockIdx.x * 32 + lane) * V;
-    const int y = 1 + (int)(blockIdx.y * WY + threadIdx.y);
-    if (y > g.ny) return;  // uniform over the warp
-    const int k0 = 1 + (int)blockIdx.z * kchunk;
-    if (k0 > g.nz) return;
-    const int k1 = min(g.nz, k0 + kchunk - 1);
-
-    // the lane's vector lies inside the row allocation (needed for shuffles even
-    // when none of its cells is interior)
-    const bool loadable = (x0 + V) <= g.px;
-    bool interior[V];
-    bool all_interior = true;
-#pragma unroll
-    for (int e = 0; e < V; ++e) {
-        interior[e] = loadable && (x0 + e >= 1) && (x0 + e <= g.nx);
-        all_interior = all_interior && interior[e];
-    }
-    const bool left_ok = (x0 >= 1);
-    const bool right_ok = (x0 + V) < g.px;
-
-    const long long row = g.lin(loadable ? x0 : 0, y, 0);
     const C c6 = Tr::sixth();
+    auto add = [](int idx, C a, C b) -> C {
+        if constexpr (NEMU > 0) {
+            if (idx < NEMU) return add_pos_exact(a, b);
+        }
+        return Tr::add(a, b);
+    };
 
     C dn[V], ct[V], up[V], no[V], so[V];
     load_vec<Tr, V>(A + row + g.plane * (k0 - 1), loadable, dn);
@@ -79,11 +68,11 @@ __global__ void __launch_bounds__(32 * WY)
         for (int e = 0; e < V; ++e) {
             const C l = (e == 0) ? left : ct[e - 1];
             const C r = (e == V - 1) ? right : ct[e + 1];
-            C s = Tr::add(l, r);
-            s = Tr::add(s, no[e]);
-            s = Tr::add(s, so[e]);
-            s = Tr::add(s, dn[e]);
-            s = Tr::add(s, up[e]);
+            C s = add(0, l, r);
+            s = add(1, s, no[e]);
+            s = add(2, s, so[e]);
+            s = add(3, s, dn[e]);
+            s = add(4, s, up[e]);
             outv.v[e] = Tr::st(Tr::mul(s, c6));
         }
         if (all_interior) {
@@ -99,6 +88,45 @@ __global__ void __launch_bounds__(32 * WY)
             ct[e] = up[e];
         }
     }
+}
+
+// `fast` (FP64, NEMU > 0): device flag written by range_check_kernel; when it is
+// set every value of A lies in [2^-1000, 2^1000], and by the maximum principle of
+// the averaging sweep so does every later value, so the emulated additions are
+// valid for the whole call.
+template <class Tr, int V, int WY, int NEMU>
+__global__ void __launch_bounds__(32 * WY)
+    plain_sweep_kernel(const typename Tr::S* __restrict__ A, typename Tr::S* __restrict__ B,
+                       const Geom g, const int kchunk, const int* __restrict__ fast) {
+    constexpr int XOFF = (V == 1) ? 1 : 0;
+    const int lane = threadIdx.x;
+    const int x0 = XOFF + (int)(blockIdx.x * 32 + lane) * V;
+    const int y = 1 + (int)(blockIdx.y * WY + threadIdx.y);
+    if (y > g.ny) return;  // uniform over the warp
+    const int k0 = 1 + (int)blockIdx.z * kchunk;
+    if (k0 > g.nz) return;
+    const int k1 = min(g.nz, k0 + kchunk - 1);
+
+    // the lane's vector lies inside the row allocation (needed for shuffles even
+    // when none of its cells is interior)
+    const bool loadable = (x0 + V) <= g.px;
+    bool interior[V];
+    bool all_interior = true;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        interior[e] = loadable && (x0 + e >= 1) && (x0 + e <= g.nx);
+        all_interior = all_interior && interior[e];
+    }
+    const bool left_ok = (x0 >= 1);
+    const bool right_ok = (x0 + V) < g.px;
+    const long long row = g.lin(loadable ? x0 : 0, y, 0);
+
+    if (NEMU > 0 && fast != nullptr && *fast)
+        plain_march<Tr, V, NEMU>(A, B, g, k0, k1, x0, y, lane, loadable, interior, all_interior,
+                                 left_ok, right_ok, row);
+    else
+        plain_march<Tr, V, 0>(A, B, g, k0, k1, x0, y, lane, loadable, interior, all_interior,
+                              left_ok, right_ok, row);
 }
 
 }  // namespace jac

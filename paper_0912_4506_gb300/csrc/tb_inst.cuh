@@ -14,12 +14,12 @@ cudaError_t tb_launch(const CUtensorMap& map, const TBArgs& a, dim3 grid, cudaSt
     return cudaGetLastError();
 }
 
-template <class TR, int V, int WY>
+template <class TR, int V, int WY, int NEMU>
 cudaError_t plain_launch(const void* A, void* B, const Geom& g, int kchunk, dim3 grid,
-                         cudaStream_t st) {
+                         const int* fast, cudaStream_t st) {
     using S = typename TR::S;
-    plain_sweep_kernel<TR, V, WY><<<grid, dim3(32, WY), 0, st>>>(
-        static_cast<const S*>(A), static_cast<S*>(B), g, kchunk);
+    plain_sweep_kernel<TR, V, WY, NEMU><<<grid, dim3(32, WY), 0, st>>>(
+        static_cast<const S*>(A), static_cast<S*>(B), g, kchunk, fast);
     return cudaGetLastError();
 }
 
@@ -30,9 +30,9 @@ cudaError_t plain_launch(const void* A, void* B, const Geom& g, int kchunk, dim3
      &::jac::tb_launch<TR, V, NW, T, MODE, NS>,                                          \
      reinterpret_cast<const void*>(&::jac::tb_sweep_kernel<TR, V, NW, T, MODE, NS>)}
 
-#define JAC_PLAIN(TR, V, WY) \
-    {TR::kDtype, V, WY, &::jac::plain_launch<TR, V, WY>, \
-     reinterpret_cast<const void*>(&::jac::plain_sweep_kernel<TR, V, WY>)}
+#define JAC_PLAIN(TR, V, WY, NEMU) \
+    {TR::kDtype, V, WY, NEMU, &::jac::plain_launch<TR, V, WY, NEMU>, \
+     reinterpret_cast<const void*>(&::jac::plain_sweep_kernel<TR, V, WY, NEMU>)}
 
 #define JAC_TABLE(NAME, ARR)                                  \
     const TBEntry* NAME(int* n) {                             \

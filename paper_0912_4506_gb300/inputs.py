@@ -145,3 +145,24 @@ def to_dtype(a64, dtype, px=None):
     w = min(px, src.shape[2])
     out[:, :, :w] = src[:, :, :w]
     return out
+
+
+def laplace_boundary_torch(nx, ny, nz, dtype=None, device="cuda", px=None):
+    """The Laplace-problem grid of `laplace_boundary_f64`, built directly on a
+    torch device (for grids too large to stage through host memory): returns a
+    (nz+2, ny+2, px) float64 tensor, boundary u = x^2 - y^2 + 0.5 z, interior 0."""
+    import torch
+    px = nx + 2 if px is None else px
+    out = torch.zeros((nz + 2, ny + 2, px), dtype=torch.float64, device=device)
+    i = torch.arange(nx + 2, dtype=torch.float64, device=device)
+    j = torch.arange(ny + 2, dtype=torch.float64, device=device)
+    for k in range(nz + 2):
+        plane = (i * i)[None, :] - (j * j)[:, None] + 0.5 * k
+        if k == 0 or k == nz + 1:
+            out[k, :, :nx + 2] = plane
+        else:
+            out[k, 0, :nx + 2] = plane[0]
+            out[k, ny + 1, :nx + 2] = plane[ny + 1]
+            out[k, 1:ny + 1, 0] = plane[1:ny + 1, 0]
+            out[k, 1:ny + 1, nx + 1] = plane[1:ny + 1, nx + 1]
+    return out

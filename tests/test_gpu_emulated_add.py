@@ -1,0 +1,109 @@
+"""The integer-pipe FP64 addition used by the plain FP64 sweep equals the FP64
+unit (IEEE-754 round-to-nearest-even) bit for bit, on random pairs across
+exponent differences 0..40 and on constructed ties, carries and boundaries;
+and the sweep with it stays bit-exact, also when negative values force the
+FP64-unit path."""
+import numpy as np
+import pytest
+
+import oracle
+from tests.helpers import make_grid, to_dev, to_host
+
+pytestmark = pytest.mark.gpu
+
+
+def _gpu_add(a, b):
+    import torch
+    from paper_0912_4506_gb300 import _lib
+    ta = torch.from_numpy(a).cuda()
+    tb = torch.from_numpy(b).cuda()
+    out = torch.empty_like(ta)
+    _lib.jacobi_emulated_add(ta.data_ptr(), tb.data_ptr(), out.data_ptr(), a.size,
+                             torch.cuda.current_stream().cuda_stream)
+    return out.cpu().numpy()
+
+
+def _bits(x):
+    return x.view(np.uint64)
+
+
+def test_random_pairs_all_exponent_gaps():
+    rng = np.random.default_rng(0)
+    n = 4_000_000
+    m1 = rng.integers(0, 1 << 52, n, dtype=np.uint64)
+    m2 = rng.integers(0, 1 << 52, n, dtype=np.uint64)
+    e1 = rng.integers(900, 1100, n, dtype=np.uint64)
+    gap = rng.integers(0, 41, n, dtype=np.uint64)
+    e2 = e1 - np.minimum(gap, e1 - 1)
+    a = ((e1 << np.uint64(52)) | m1).view(np.float64)
+    b = ((e2 << np.uint64(52)) | m2).view(np.float64)
+    swap = rng.random(n) < 0.5
+    a, b = np.where(swap, b, a), np.where(swap, a, b)
+    got = _gpu_add(a, b)
+    want = a + b
+    assert np.array_equal(_bits(got), _bits(want))
+
+
+def test_constructed_edge_cases():
+    cases = []
+    one = 1.0
+    ulp = 2.0 ** -52
+    for k in range(0, 60):
+        h = 2.0 ** -k
+        cases += [(one, h), (one + ulp, h), (2 - ulp, h), (2 - ulp, 2 - ulp), (one, h * (1 + ulp)),
+                  (one + 3 * ulp, h), (1.5, h * 1.5), (np.nextafter(2.0, 0), h)]
+    # exact ties at every shift within the integer path
+    for d in range(1, 32):
+        cases.append((1.0 + ulp, 2.0 ** (-52 - 1)))          # half ulp: tie to even
+        cases.append((1.0, 2.0 ** (-52 - 1) * (1 + 2.0 ** -(d % 40))))
+    cases += [(3.0, 5.0), (0.75, 0.25), (1e-300, 1e-300), (1e300, 1e300), (6.0, 2.0 ** -30)]
+    a = np.array([c[0] for c in cases] + [c[1] for c in cases])
+    b = np.array([c[1] for c in cases] + [c[0] for c in cases])
+    got = _gpu_add(a, b)
+    assert np.array_equal(_bits(got), _bits(a + b))
+
+
+def test_uniform_unit_interval_sums():
+    rng = np.random.default_rng(1)
+    n = 2_000_000
+    s = np.zeros(n)
+    terms = rng.random((6, n))
+    for t in terms:  # the partial sums of Eq. 1 on U[0,1) data
+        got = _gpu_add(np.where(s == 0, t, s), np.where(s == 0, 0.5, t))
+        want = np.where(s == 0, t, s) + np.where(s == 0, 0.5, t)
+        assert np.array_equal(_bits(got), _bits(want))
+        s = want
+
+
+def test_sweep_with_negative_values_uses_fp64_unit_and_stays_exact():
+    from paper_0912_4506_gb300 import api, inputs
+    nx, ny, nz = 40, 33, 21
+    u0 = inputs.laplace_boundary_f64(nx, ny, nz, px=inputs.row_pitch(nx, "f64"))
+    u0[1:-1, 1:-1, 1:nx + 1] = np.random.default_rng(2).random((nz, ny, nx)) - 0.5
+    j = api.Jacobi(api.as_grid(to_dev(u0, "f64"), nx))
+    got = to_host(j.sweep(9, 1, api.JAC_KERNEL_PLAIN), "f64")
+    j.close()
+    assert np.array_equal(got, oracle.sweeps(u0, 9, nx=nx)[:, :, :nx + 2])
+
+
+@pytest.mark.parametrize("nemu", [0, 1, 2, 3, 4, 5])
+def test_every_emulation_split_bit_exact(nemu, monkeypatch):
+    """Run each split in a fresh process (the split is read once per process)."""
+    import subprocess
+    import sys
+    import os
+    code = (
+        "import sys; sys.path.insert(0, %r)\n"
+        "import numpy as np, oracle\n"
+        "from paper_0912_4506_gb300 import api\n"
+        "from tests.helpers import make_grid, to_dev, to_host\n"
+        "a = make_grid(77, 45, 30, 'f64')\n"
+        "j = api.Jacobi(api.as_grid(to_dev(a, 'f64'), 77))\n"
+        "assert j.plan(5, 1, api.JAC_KERNEL_PLAIN)['emu_adds'] == %d\n"
+        "got = to_host(j.sweep(5, 1, api.JAC_KERNEL_PLAIN), 'f64')\n"
+        "assert np.array_equal(got, oracle.sweeps(a, 5, nx=77)[:, :, :79])\n"
+        "print('ok')\n" % (os.path.dirname(os.path.dirname(os.path.abspath(__file__))), nemu))
+    env = dict(os.environ, JACOBI_F64_EMU=str(nemu))
+    r = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0 and "ok" in r.stdout, r.stderr[-3000:]

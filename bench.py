@@ -36,8 +36,22 @@ DP_OPS_PER_CLK_PER_SM = 2   # GB300 FP64: 1.25 TFLOP/s nominal with FMA counted 
 ALGO_BYTES_PER_LUP = {"f64": 16, "f32": 8, "bf16": 4}
 
 # DRAM bytes per launch of the dominant kernel from the ncu captures committed
-# under profiles/ (None when no capture of the current kernel exists).
-TRAFFIC_PER_LAUNCH = {}
+# under profiles/ (None when no capture of the current kernel exists).  The 512^3
+# figure scales the 384^3 capture by the lattice-site updates (traffic is
+# proportional to them: 16 B per update, no re-reads).
+TRAFFIC_PER_LAUNCH = {
+    # profiles/plain_sweep_f64_emu5_384cubed.md: 477.6 MB read + 412.8 MB written
+    # for 384^3 (56.6 M updates) -> x (512/384)^3
+    "plain_sweep_kernel<F64,emu=5>": round((477572352 + 412830976) * (512 / 384) ** 3),
+}
+
+# Pipe cost of the FP64 plain sweep with 2.5 of its 5 additions on the integer
+# pipes (profiles/plain_sweep_f64_emu5_384cubed.md): FP64 pipe 3.5 ops per update
+# at 2 ops/clk/SM = 1.75 SM-cycles per update; the integer ALU pipe is busy 1.81
+# SM-cycles per update (ncu sm__pipe_alu_cycles_active, 74.8 % of 898.8 k cycles
+# per SMSP for 93.1 k updates per SMSP, 4 SMSPs per SM).  The binding pipe sets
+# the ceiling: SMs x clock / max(1.75, 1.81).
+F64_EMU_SM_CYCLES_PER_LUP = {"fp64": 1.75, "alu": 1.806}
 
 
 def parse():
@@ -442,22 +456,35 @@ def run_ours(args):
         return
 
     pk, pk_src = peaks()
-    kname = "plain_sweep_kernel<F64>" if plan["kernel"] == 1 else f"tb_sweep_kernel<F64,T={plan['t']}>"
+    emu = plan.get("emu_adds", 0)
+    kname = (f"plain_sweep_kernel<F64,emu={emu}>" if plan["kernel"] == 1
+             else f"tb_sweep_kernel<F64,T={plan['t']}>")
     launch_s = ms_step / 1e3 / launches_per_step
     sweeps_per_launch = NSWEEPS / launches_per_step
     if plan["kernel"] == 1:
         mhz = pk.get("sm_max_mhz", 2070.0)
-        peak_tf = DP_OPS_PER_CLK_PER_SM * SM_COUNT * mhz * 1e6 / 1e12
-        achieved = DP_OPS_PER_LUP * NX * NY * NZ * sweeps_per_launch / launch_s / 1e12
-        roof = {"bound": "alu", "achieved": round(achieved, 4), "peak": round(peak_tf, 4),
-                "unit": "TFLOP/s", "frac": round(achieved / peak_tf, 4),
-                "traffic": TRAFFIC_PER_LAUNCH.get(kname),
-                "kernel": kname,
-                "peak_source": f"FP64 pipe: {DP_OPS_PER_CLK_PER_SM} DP ops/clk/SM x "
-                               f"{SM_COUNT} SMs x {mhz:.0f} MHz (derived from unit counts and "
-                               "the maximum SM clock)",
-                "hbm_frac": round(ALGO_BYTES_PER_LUP["f64"] * NX * NY * NZ * sweeps_per_launch
-                                  / launch_s / 1e9 / pk["hbm_gbs"], 4)}
+        lups_launch = NX * NY * NZ * sweeps_per_launch
+        achieved_glups = lups_launch / launch_s / 1e9
+        fp64_only = DP_OPS_PER_CLK_PER_SM * SM_COUNT * mhz * 1e6 / DP_OPS_PER_LUP / 1e9
+        if emu == 5:
+            cyc = max(F64_EMU_SM_CYCLES_PER_LUP.values())
+            peak_glups = SM_COUNT * mhz * 1e6 / cyc / 1e9
+            src = ("two-pipe ceiling: 152 SMs x %.0f MHz / max(FP64 pipe 1.75, integer ALU pipe "
+                   "1.81) SM-cycles per update (FP64 unit 2 ops/clk/SM; ALU cycles from ncu, "
+                   "profiles/plain_sweep_f64_emu5_384cubed.md)" % mhz)
+        else:
+            peak_glups = fp64_only
+            src = ("FP64 pipe: %d DP ops/clk/SM x %d SMs x %.0f MHz / 6 ops per update"
+                   % (DP_OPS_PER_CLK_PER_SM, SM_COUNT, mhz))
+        roof = {"bound": "alu", "achieved": round(achieved_glups, 3),
+                "peak": round(peak_glups, 3), "unit": "GLUP/s",
+                "frac": round(achieved_glups / peak_glups, 4),
+                "traffic": TRAFFIC_PER_LAUNCH.get(kname), "kernel": kname,
+                "peak_source": src,
+                "fp64_unit_only_peak": round(fp64_only, 3),
+                "frac_vs_fp64_unit_only": round(achieved_glups / fp64_only, 4),
+                "hbm_frac": round(ALGO_BYTES_PER_LUP["f64"] * lups_launch / launch_s / 1e9
+                                  / pk["hbm_gbs"], 4)}
     else:
         bytes_launch = ALGO_BYTES_PER_LUP["f64"] * NX * NY * NZ
         achieved = bytes_launch / launch_s / 1e9

@@ -83,7 +83,8 @@ typedef struct {
     int smem_bytes;        /* dynamic shared memory per CTA                       */
     int grid_x, grid_y, grid_z;
     int emu_adds;          /* FP64 plain sweep: additions done on the integer pipes
-                              when the grid's values allow it (see jacobi_emulated_add) */
+                              when the grid's values allow it (see jacobi_emulated_add),
+                              in half additions per plane: 5 = 2 and 3 on alternate planes */
 } jacobi_plan_info;
 
 /*

@@ -18,7 +18,7 @@
 using namespace jac;
 
 namespace {
-constexpr int kDefaultF64Emu = 2;
+constexpr int kDefaultF64Emu = 5;  // half additions per plane (2.5 of 5)
 }
 
 struct jacobi_s {
@@ -114,8 +114,8 @@ void ensure_attrs(const std::vector<TBEntry>& tab, int device) {
     }
 }
 
-// Number of the five additions the FP64 plain sweep does on the integer pipes
-// (when the range check allows it); JACOBI_F64_EMU overrides (0..5).
+// Additions the FP64 plain sweep does on the integer pipes when the range check
+// allows it, in half additions per plane (0..8); JACOBI_F64_EMU overrides.
 int f64_emu_count() {
     static int n = -1;
     static std::once_flag once;
@@ -123,7 +123,7 @@ int f64_emu_count() {
         n = kDefaultF64Emu;
         if (const char* e = getenv("JACOBI_F64_EMU")) {
             const int v = atoi(e);
-            if (v >= 0 && v <= 5) n = v;
+            if (v >= 0 && v <= 8) n = v;
         }
     });
     return n;

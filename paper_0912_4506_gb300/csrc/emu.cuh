@@ -9,12 +9,13 @@
 // the sweep stays bit-exact whichever additions are emulated.
 //
 // Method (written from the definition of binary64 and of rounding to nearest
-// even): take the operand X with the larger exponent and the other, Y (for
-// positive doubles the bit patterns order like the values), align Y's 53-bit significand to X's
-// exponent keeping 9 extra low bits plus a sticky bit for everything shifted
-// out, add, and round the 54- or 55-bit sum back to 53 bits with the usual
-// "add half-minus-one plus the kept LSB, then shift" step; the exponent follows
-// from the carry.  Exponent differences above 31 (the smaller operand then
+// even): take the operand X with the larger exponent and the other, Y; shift
+// Y's 53-bit significand right by the exponent difference, keeping the bits
+// shifted out as a 32-bit fraction; add; renormalise by one bit on a carry
+// (folding the lost bit into a sticky bit); round to 53 bits by comparing the
+// fraction with one half (ties to the even significand); the exponent follows
+// from the carry, and a rounding carry to 2^53 moves into the exponent field
+// by itself.  Exponent differences above 31 (the smaller operand then
 // only affects the sticky bit, and such lanes are rare) go to the FP64 unit.
 // Operands must be positive normal numbers whose sum stays finite; the caller
 // guarantees that (see range_check_kernel).
@@ -48,16 +49,22 @@ __device__ __forceinline__ double add_pos_exact(double a, double b) {
     const uint32_t d = ex - (uint32_t)(Y >> 52);
     const uint32_t dd = d > 31u ? 31u : d;  // keeps the integer path defined
     const unsigned long long kMant = 0x000FFFFFFFFFFFFFull, kHidden = 0x0010000000000000ull;
-    const unsigned long long mx = ((X & kMant) | kHidden) << 9;
-    const unsigned long long my = ((Y & kMant) | kHidden) << 9;
-    // bits of my shifted out by dd (only its low word can lose bits, dd <= 31)
-    const uint32_t sticky = shl32((uint32_t)my, 32u - dd) != 0u ? 1u : 0u;
-    const unsigned long long S = mx + ((my >> dd) | sticky);  // in [2^61, 2^63)
-    const uint32_t c = (uint32_t)(S >> 62);                    // carry out of the add
-    const uint32_t sh = 9u + c;
-    const unsigned long long lsb = (S >> sh) & 1ull;
-    const unsigned long long R = (S + (((unsigned long long)0x100u << c) - 1ull) + lsb) >> sh;
-    double r = __longlong_as_double((long long)((((unsigned long long)(ex + c - 1u)) << 52) + R));
+    const unsigned long long mx = (X & kMant) | kHidden;  // 53-bit significands
+    const unsigned long long my = (Y & kMant) | kHidden;
+    // exact sum = S + F / 2^32: S integer, F the 32-bit fraction of my / 2^dd
+    // (dd <= 31, so the bits shifted out fit in the low word)
+    const uint32_t F = shl32((uint32_t)my, 32u - dd);
+    const unsigned long long S = mx + (my >> dd);           // in [2^52, 2^54)
+    const uint32_t c = (uint32_t)(S >> 53);                 // carry: renormalise by 1
+    const unsigned long long Sn = S >> c;
+    // fraction after the renormalisation, with everything below bit 0 folded
+    // into bit 0 (a sticky bit): it still compares with 2^31 exactly
+    const uint32_t Fc = c ? (((uint32_t)S << 31) | (F >> 1) | (F & 1u)) : F;
+    // round to nearest, ties to even: up when Fc > 2^31, or Fc == 2^31 and Sn odd
+    const uint32_t up =
+        (uint32_t)(((unsigned long long)Fc + 0x7FFFFFFFull + (Sn & 1ull)) >> 32);
+    const unsigned long long M = Sn + up;  // may reach 2^53: the exponent absorbs it
+    double r = __longlong_as_double((long long)((((unsigned long long)(ex + c - 1u)) << 52) + M));
     if (__any_sync(__activemask(), d > 31u)) {
         if (d > 31u) r = add_fp64_unit(a, b);
     }

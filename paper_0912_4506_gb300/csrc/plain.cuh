@@ -30,7 +30,9 @@ __device__ __forceinline__ void load_vec(const typename Tr::S* __restrict__ p, b
 }
 
 // The sweep of one chunk, with the first NEMU of the five additions done by
-// add_pos_exact (FP64 only; NEMU = 0: all on the FP64 unit).
+// add_pos_exact (FP64 only; NEMU = 0: all on the FP64 unit).  NEMU is counted in
+// half additions: an odd NEMU does NEMU/2 on even planes and NEMU/2 + 1 on odd
+// planes, which balances the FP64 and integer pipes between whole splits.
 template <class Tr, int V, int NEMU>
 __device__ __forceinline__ void plain_march(const typename Tr::S* __restrict__ A,
                                             typename Tr::S* __restrict__ B, const Geom& g,
@@ -42,9 +44,9 @@ __device__ __forceinline__ void plain_march(const typename Tr::S* __restrict__ A
     using C = typename Tr::C;
     const unsigned FULL = 0xffffffffu;
     const C c6 = Tr::sixth();
-    auto add = [](int idx, C a, C b) -> C {
+    auto add = [](int idx, int nemu, C a, C b) -> C {
         if constexpr (NEMU > 0) {
-            if (idx < NEMU) return add_pos_exact(a, b);
+            if (idx < nemu) return add_pos_exact(a, b);
         }
         return Tr::add(a, b);
     };
@@ -53,7 +55,7 @@ __device__ __forceinline__ void plain_march(const typename Tr::S* __restrict__ A
     load_vec<Tr, V>(A + row + g.plane * (k0 - 1), loadable, dn);
     load_vec<Tr, V>(A + row + g.plane * k0, loadable, ct);
 
-    for (int k = k0; k <= k1; ++k) {
+    auto plane_step = [&](int k, int nemu) {
         const long long base = row + g.plane * k;
         load_vec<Tr, V>(A + base + g.plane, loadable, up);
         load_vec<Tr, V>(A + base - g.px, loadable, no);
@@ -68,11 +70,11 @@ __device__ __forceinline__ void plain_march(const typename Tr::S* __restrict__ A
         for (int e = 0; e < V; ++e) {
             const C l = (e == 0) ? left : ct[e - 1];
             const C r = (e == V - 1) ? right : ct[e + 1];
-            C s = add(0, l, r);
-            s = add(1, s, no[e]);
-            s = add(2, s, so[e]);
-            s = add(3, s, dn[e]);
-            s = add(4, s, up[e]);
+            C s = add(0, nemu, l, r);
+            s = add(1, nemu, s, no[e]);
+            s = add(2, nemu, s, so[e]);
+            s = add(3, nemu, s, dn[e]);
+            s = add(4, nemu, s, up[e]);
             outv.v[e] = Tr::st(Tr::mul(s, c6));
         }
         if (all_interior) {
@@ -87,7 +89,15 @@ __device__ __forceinline__ void plain_march(const typename Tr::S* __restrict__ A
             dn[e] = ct[e];
             ct[e] = up[e];
         }
+    };
+    constexpr int kEven = NEMU / 2, kOdd = (NEMU + 1) / 2;
+    int k = k0;
+#pragma unroll 1
+    for (; k + 1 <= k1; k += 2) {
+        plane_step(k, kEven);
+        plane_step(k + 1, kOdd);
     }
+    if (k <= k1) plane_step(k, kEven);
 }
 
 // `fast` (FP64, NEMU > 0): device flag written by range_check_kernel; when it is

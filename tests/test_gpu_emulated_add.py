@@ -86,7 +86,7 @@ def test_sweep_with_negative_values_uses_fp64_unit_and_stays_exact():
     assert np.array_equal(got, oracle.sweeps(u0, 9, nx=nx)[:, :, :nx + 2])
 
 
-@pytest.mark.parametrize("nemu", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("nemu", [0, 2, 4, 5, 6, 7, 8])
 def test_every_emulation_split_bit_exact(nemu, monkeypatch):
     """Run each split in a fresh process (the split is read once per process)."""
     import subprocess

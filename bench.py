@@ -139,6 +139,21 @@ def dist_setup():
     return world, rank, local
 
 
+def replica_throughput(ms_local, lups_per_rank, device="cpu"):
+    """Whole-job throughput of N independent replicas: the slowest rank's time
+    (max over ranks, all_reduce MAX) and all ranks' lattice-site updates over it.
+    Returns (ms_max, GLUP/s).  Single process: (ms_local, lups / ms_local)."""
+    import torch
+    import torch.distributed as dist
+    world = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    ms = float(ms_local)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, lups_per_rank * world / (ms / 1e3) / 1e9
+
+
 def make_input(dtype="f64"):
     from paper_0912_4506_gb300 import inputs
     a = inputs.uniform_grid_f64(NX, NY, NZ, px=inputs.row_pitch(NX, dtype))
@@ -420,13 +435,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
-    if world > 1:
-        tt = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
-    ms_step = ms / args.steps
     lups = NX * NY * NZ * NSWEEPS
+    ms, _ = replica_throughput(e0.elapsed_time(e1), lups * args.steps, dev)
+    ms_step = ms / args.steps
     value = lups * world / (ms_step / 1e3) / 1e9
 
     # end to end through the C ABI on host buffers: upload, 100 sweeps, download
@@ -443,11 +454,7 @@ def run_ours(args):
     e3.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ms_e2e = e2.elapsed_time(e3)
-    if world > 1:
-        tt = torch.tensor([ms_e2e], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms_e2e = float(tt.item())
+    ms_e2e, _ = replica_throughput(e2.elapsed_time(e3), lups * args.steps, dev)
     e2e_value = lups * world / (ms_e2e / args.steps / 1e3) / 1e9
     nbytes = host_in.numel() * host_in.element_size()
 
@@ -527,10 +534,55 @@ def run_ours(args):
 
 def run_case(args):
     """One kernel configuration only (for profiler captures): args.steps calls of
-    args.sweeps sweeps on a size^3 grid of args.dtype."""
+    args.sweeps sweeps on a size^3 grid of args.dtype (--case residual: args.steps
+    FP64 residual steps with an args.dtype correction)."""
     import torch
     from paper_0912_4506_gb300 import api, inputs
     n = args.size
+    if args.case == "adjoint":
+        px = inputs.row_pitch(n, args.dtype)
+        W = api.from_numpy(inputs.to_dtype(inputs.normal_grid_f64(n, n, n), args.dtype, px=px),
+                           n, "cuda")
+        lam = api.alloc_like(W)
+        lam[1:-1, 1:-1, 1:-1].copy_(W[1:-1, 1:-1, 1:-1])
+        gb = api.alloc_like(W)
+        j = api.Jacobi(lam)
+        for _ in range(args.warmup):
+            j.adjoint(gb, args.sweeps, args.t)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            j.adjoint(gb, args.sweeps, args.t)
+        e1.record()
+        torch.cuda.synchronize()
+        j.check()
+        ms = e0.elapsed_time(e1) / args.steps
+        print(json.dumps({"case": "adjoint", "dtype": args.dtype, "t": args.t, "size": n,
+                          "sweeps": args.sweeps, "ms": round(ms, 4),
+                          "glups": round(n ** 3 * args.sweeps / ms / 1e6, 2)}), flush=True)
+        j.close()
+        return
+    if args.case == "residual":
+        u0 = api.as_grid(inputs.laplace_boundary_torch(n, n, n, device="cuda"), n)
+        r = api.Refiner(u0, args.dtype)
+        u = r.u
+        for _ in range(args.warmup):
+            api.residual_accumulate(u[0], u[1], r.e0, r.rho)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            api.residual_accumulate(u[0], u[1], r.e0, r.rho)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        print(json.dumps({"case": "residual", "dtype": args.dtype, "size": n, "ms": round(ms, 4),
+                          "gcells_per_s": round(n ** 3 / ms / 1e6, 2)}), flush=True)
+        r.close()
+        return
     a = inputs.to_dtype(inputs.uniform_grid_f64(n, n, n), args.dtype,
                         px=inputs.row_pitch(n, args.dtype))
     j = api.Jacobi(api.from_numpy(a, n, "cuda"))

@@ -108,74 +108,93 @@ __global__ void emulated_add_kernel(const double* __restrict__ a, const double* 
 //     u_out = u'
 //     rho   = ((((( u'[i-1] + u'[i+1]) + u'[j-1]) + u'[j+1]) + u'[k-1]) + u'[k+1]) - 6.0*u'
 // in FP64 (product rounded before the subtraction), rho rounded to the low
-// precision.  u' of a neighbour is recomputed from u_in and e instead of being
-// read back from u_out, so the kernel needs no grid-wide barrier and gives the
-// same bits as "accumulate everywhere, then take the residual".
-// Thread layout: lane -> x (interior-aligned, one cell), warp -> y, k marched.
+// precision.  The kernel is bound by the FP64 pipe (2 ops/clk/SM on GB300), so
+// u' is formed once per cell: a CTA of RES_ROWS + 2 warps covers 32 x-cells of
+// RES_ROWS rows plus one halo row above and below; each warp forms u' for its
+// row of the plane streaming in, keeps the k-1, k, k+1 values in registers, and
+// shares the k plane through shared memory (y-neighbours) and shuffles (x); the
+// halo warps only form u'.  Same bits as "accumulate everywhere, then take the
+// residual" (u' of a cell is the same FP64 sum wherever it is formed).
+constexpr int RES_ROWS = 8;
+
 template <class Lo>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__((RES_ROWS + 2) * 32)
     residual_kernel(const double* __restrict__ u_in, double* __restrict__ u_out, const Geom gu,
                     const typename Lo::S* __restrict__ e, typename Lo::S* __restrict__ rho,
-                    const Geom gl) {
+                    const Geom gl, const int kchunk) {
+    __shared__ double s_u[2][RES_ROWS + 2][32];
     const unsigned FULL = 0xffffffffu;
-    const int lane = threadIdx.x;
-    const int x = 1 + (int)(blockIdx.x * 32 + lane);
-    const int y = 1 + (int)(blockIdx.y * blockDim.y + threadIdx.y);
-    if (y > gu.ny) return;  // uniform over the warp
-    const bool act = x <= gu.nx;
-    const int xc = act ? x : gu.nx;  // clamped for address arithmetic
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // w = 0 and RES_ROWS+1: halo
+    const int x = 1 + (int)blockIdx.x * 32 + lane;
+    const int y = (int)blockIdx.y * RES_ROWS + w;  // row of this warp (0 .. ny+1 possible)
+    const int k0 = 1 + (int)blockIdx.z * kchunk;
+    const int k1 = min(gu.nz, k0 + kchunk - 1);
+    const int xc = min(x, gu.nx + 1);  // clamped column (loads stay inside the array)
+    const int yc = min(y, gu.ny + 1);
+    const bool row_in = y >= 1 && y <= gu.ny;
+    const bool cell_in = row_in && x <= gu.nx;      // interior in x and y
+    const bool compute = w >= 1 && w <= RES_ROWS && cell_in;
+    const int ktop = gu.nz + 1;
 
-    // u' at (xx, yy, kk); interior test per cell
-    auto unew = [&](int xx, int yy, int kk) -> double {
-        const double u = __ldg(u_in + gu.lin(xx, yy, kk));
-        const bool in = (xx >= 1) && (xx <= gu.nx) && (yy >= 1) && (yy <= gu.ny) && (kk >= 1) &&
-                        (kk <= gu.nz);
-        if (!in) return u;
-        return __dadd_rn(u, (double)Lo::ld(__ldg(e + gl.lin(xx, yy, kk))));
+    // u' of this lane's column at plane kk (boundary planes and cells: u_in)
+    auto uprime = [&](int xx, int kk) -> double {
+        const double u = __ldg(u_in + gu.lin(xx, yc, kk));
+        const bool in = row_in && xx >= 1 && xx <= gu.nx && kk >= 1 && kk <= gu.nz;
+        return in ? __dadd_rn(u, (double)Lo::ld(__ldg(e + gl.lin(xx, yc, kk)))) : u;
     };
-
-    double dn = unew(xc, y, 0);
-    double ct = unew(xc, y, 1);
-    for (int k = 1; k <= gu.nz; ++k) {
-        const double up = unew(xc, y, k + 1);
-        const double no = unew(xc, y - 1, k);
-        const double so = unew(xc, y + 1, k);
+    double dn = uprime(xc, k0 - 1);
+    double ct = uprime(xc, k0);
+    double up = uprime(xc, min(k0 + 1, ktop));
+    int buf = 0;
+    s_u[buf][w][lane] = ct;
+    __syncthreads();
+    for (int k = k0; k <= k1; ++k) {
+        // next plane first (its loads overlap this step's arithmetic)
+        const double up2 = uprime(xc, min(k + 2, ktop));
         double left = __shfl_up_sync(FULL, ct, 1);
         double right = __shfl_down_sync(FULL, ct, 1);
-        if (lane == 0) left = unew(xc - 1, y, k);
-        if (lane == 31 || x == gu.nx) right = unew(xc + 1, y, k);
-        if (act) {
+        if (lane == 0) left = uprime(x - 1, k);
+        if (lane == 31 || x == gu.nx) right = uprime(min(x + 1, gu.nx + 1), k);
+        if (compute) {
             double s = __dadd_rn(left, right);
-            s = __dadd_rn(s, no);
-            s = __dadd_rn(s, so);
+            s = __dadd_rn(s, s_u[buf][w - 1][lane]);
+            s = __dadd_rn(s, s_u[buf][w + 1][lane]);
             s = __dadd_rn(s, dn);
             s = __dadd_rn(s, up);
-            const double six_u = __dmul_rn(6.0, ct);
-            const double r = __dsub_rn(s, six_u);
+            const double r = __dsub_rn(s, __dmul_rn(6.0, ct));
             u_out[gu.lin(x, y, k)] = ct;
             rho[gl.lin(x, y, k)] = Lo::st((typename Lo::C)r);
         }
         dn = ct;
         ct = up;
+        up = up2;
+        buf ^= 1;
+        s_u[buf][w][lane] = ct;
+        __syncthreads();
     }
 }
 
 cudaError_t launch_residual(const double* u_in, double* u_out, const Geom& gu, const void* e,
                             void* rho, int lo_dtype, const Geom& glo, cudaStream_t st) {
-    const dim3 block(32, 8);
-    const dim3 grid((gu.nx + 31) / 32, (gu.ny + 7) / 8, 1);
+    const dim3 block((RES_ROWS + 2) * 32);
+    // k-chunks of at least 16 planes, enough CTAs for several waves
+    const long long tiles = (long long)((gu.nx + 31) / 32) * ((gu.ny + RES_ROWS - 1) / RES_ROWS);
+    int chunks = (int)std::max<long long>(1, std::min<long long>(gu.nz / 16, 8192 / tiles + 1));
+    const int kchunk = (gu.nz + chunks - 1) / chunks;
+    chunks = (gu.nz + kchunk - 1) / kchunk;
+    const dim3 grid((gu.nx + 31) / 32, (gu.ny + RES_ROWS - 1) / RES_ROWS, chunks);
     if (lo_dtype == 1) {
         residual_kernel<F32><<<grid, block, 0, st>>>(u_in, u_out, gu,
                                                      static_cast<const float*>(e),
-                                                     static_cast<float*>(rho), glo);
+                                                     static_cast<float*>(rho), glo, kchunk);
     } else if (lo_dtype == 2) {
         residual_kernel<BF16><<<grid, block, 0, st>>>(u_in, u_out, gu,
                                                       static_cast<const uint16_t*>(e),
-                                                      static_cast<uint16_t*>(rho), glo);
+                                                      static_cast<uint16_t*>(rho), glo, kchunk);
     } else {
         residual_kernel<F64><<<grid, block, 0, st>>>(u_in, u_out, gu,
                                                      static_cast<const double*>(e),
-                                                     static_cast<double*>(rho), glo);
+                                                     static_cast<double*>(rho), glo, kchunk);
     }
     return cudaGetLastError();
 }

@@ -118,16 +118,6 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a
         all_out = all_out && outxy[e];
         all_in = all_in && inxy[e];
     }
-    // boundary-gradient faces touched by this thread's cells (MODE_ADJ)
-    bool face_xy = false;
-    if (MODE == MODE_ADJ) {
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-            const int x = gx0 + e;
-            face_xy = face_xy ||
-                      (outxy[e] && (x == 1 || x == g.nx || gy == 1 || gy == g.ny));
-        }
-    }
 
     if (tid == 0) {
 #pragma unroll 1
@@ -146,7 +136,9 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a
     }
 
     C r[T][3][V];                                 // per level s < T: 3 planes of level s
-    C rq[(MODE == MODE_RHS) ? T + 1 : 1][V];      // rho FIFO: rq[j] = rho at plane Zlo+m-j
+    // rho FIFO (MODE_RHS): rq[j] = rho at plane Zlo+m-j
+    constexpr int kRQ = (MODE == MODE_RHS) ? T + 1 : 1;
+    C rq[kRQ][V];
 #pragma unroll
     for (int s = 0; s < T; ++s)
 #pragma unroll
@@ -154,7 +146,7 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a
 #pragma unroll
             for (int e = 0; e < V; ++e) r[s][j][e] = C(0);
 #pragma unroll
-    for (int j = 0; j < ((MODE == MODE_RHS) ? T + 1 : 1); ++j)
+    for (int j = 0; j < kRQ; ++j)
 #pragma unroll
         for (int e = 0; e < V; ++e) rq[j][e] = C(0);
 
@@ -164,23 +156,57 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a
     S* grad = static_cast<S*>(a.grad);
     const long long rowoff = (long long)gy * g.px + gx0;  // valid only when used
     const int mycol = w * EX + lane * V;
+    auto load_rho = [&](int pr, C (&dst)[V]) {
+        const bool zinr = (pr >= 1) && (pr <= g.nz);
+        if (zinr && all_in) {
+            const Vec<S, V> q = ldg_vec<S, V>(rho + g.plane * pr + rowoff);
+#pragma unroll
+            for (int e = 0; e < V; ++e) dst[e] = Tr::ld(q.v[e]);
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                dst[e] = (zinr && inxy[e]) ? Tr::ld(rho[g.plane * pr + rowoff + e]) : C(0);
+        }
+    };
 
-    auto adj_acc = [&](const C (&v)[V], int p) {
-        if (p < kz0 || p >= kz1) return;
-        const bool zf = (p == 1) || (p == g.nz);
-        if (!face_xy && !zf) return;
+    // boundary-gradient accumulation (MODE_ADJ): face flags per cell, 4 bits each
+    // (x = 1, x = nx, y = 1, y = ny), precomputed; z faces are uniform per plane
+    uint32_t fmask = 0;
+    if (MODE == MODE_ADJ) {
 #pragma unroll
         for (int e = 0; e < V; ++e) {
-            if (!outxy[e]) continue;
             const int x = gx0 + e;
+            if (outxy[e])
+                fmask |= ((x == 1) ? 1u : 0u) | ((x == g.nx) ? 2u : 0u) | ((gy == 1) ? 4u : 0u) |
+                         ((gy == g.ny) ? 8u : 0u) | 16u;  // 16: cell owned (z faces)
+            if (e + 1 < V) fmask <<= 5;
+        }
+    }
+    constexpr uint32_t kXYFaces = 0x1EF7BDEFu & ((V >= 6) ? 0xFFFFFFFFu : ((1u << (5 * V)) - 1u));
+    const bool xy_face = (fmask & kXYFaces) != 0u;  // this thread owns an x or y face cell
+    auto adj_acc = [&](const C* v, int p) {
+        if constexpr (MODE != MODE_ADJ || !std::is_same<S, C>::value) return;
+        const bool zlo = p == 1, zhi = p == g.nz;
+        // tiles inside the interior in x and y own no x/y face: only the z faces
+        if (FAST ? !(zlo || zhi) : (!xy_face && !(zlo || zhi))) return;
+        if (p < kz0 || p >= kz1 || fmask == 0u) return;
+        C* gacc = reinterpret_cast<C*>(grad);  // the adjoint runs on FP32/FP64 grids
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const uint32_t f = (fmask >> (5 * (V - 1 - e))) & 31u;
+            if (!(f & 16u)) continue;
             const C cv = Tr::mul(c6, v[e]);
-            auto acc = [&](long long o) { grad[o] = Tr::st(Tr::add(Tr::ld(grad[o]), cv)); };
-            if (x == 1) acc(g.lin(0, gy, p));
-            if (x == g.nx) acc(g.lin(g.nx + 1, gy, p));
-            if (gy == 1) acc(g.lin(x, 0, p));
-            if (gy == g.ny) acc(g.lin(x, g.ny + 1, p));
-            if (p == 1) acc(g.lin(x, gy, 0));
-            if (p == g.nz) acc(g.lin(x, gy, g.nz + 1));
+            const int x = gx0 + e;
+            // fire-and-forget reductions: one thread owns each face cell and issues
+            // its contributions in level order, so the rounding sequence is that of
+            // grad += c*lambda_S, += c*lambda_{S-1}, ... (deterministic) without the
+            // warp waiting for a read-modify-write round trip
+            if (f & 1u) atomicAdd(gacc + g.lin(0, gy, p), cv);
+            if (f & 2u) atomicAdd(gacc + g.lin(g.nx + 1, gy, p), cv);
+            if (f & 4u) atomicAdd(gacc + g.lin(x, 0, p), cv);
+            if (f & 8u) atomicAdd(gacc + g.lin(x, g.ny + 1, p), cv);
+            if (zlo) atomicAdd(gacc + g.lin(x, gy, 0), cv);
+            if (zhi) atomicAdd(gacc + g.lin(x, gy, g.nz + 1), cv);
         }
     };
 
@@ -204,21 +230,11 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a
 #pragma unroll
             for (int e = 0; e < V; ++e) r[0][NEW][e] = Tr::ld(t.v[e]);
             if (MODE == MODE_RHS) {
-                const bool zin0 = (p0 >= 1) && (p0 <= g.nz);
 #pragma unroll
-                for (int j = ((MODE == MODE_RHS) ? T : 0); j >= 1; --j)
+                for (int j = kRQ - 1; j >= 1; --j)
 #pragma unroll
                     for (int e = 0; e < V; ++e) rq[j][e] = rq[j - 1][e];
-                if (zin0 && all_in) {
-                    const Vec<S, V> q = ldg_vec<S, V>(rho + g.plane * p0 + rowoff);
-#pragma unroll
-                    for (int e = 0; e < V; ++e) rq[0][e] = Tr::ld(q.v[e]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < V; ++e)
-                        rq[0][e] = (zin0 && inxy[e]) ? Tr::ld(rho[g.plane * p0 + rowoff + e])
-                                                     : C(0);
-                }
+                load_rho(p0, rq[0]);
             }
             if (MODE == MODE_ADJ) adj_acc(r[0][NEW], p0);
         }
@@ -246,7 +262,7 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a
                     sum = Tr::add(sum, Tr::ld(vs.v[e]));
                     sum = Tr::add(sum, r[s - 1][OLD][e]);
                     sum = Tr::add(sum, r[s - 1][NEW][e]);
-                    if (MODE == MODE_RHS) sum = Tr::add(sum, rq[s][e]);
+                    if (MODE == MODE_RHS) sum = Tr::add(sum, rq[(MODE == MODE_RHS) ? s : 0][e]);
                     const C val = Tr::rnd(Tr::mul(sum, c6));
                     out[e] = (FAST || inxy[e]) ? val : r[s - 1][CUR][e];
                 }

@@ -12,7 +12,7 @@ static const TBEntry kTB[] = {
 };
 JAC_TABLE(tb_entries_bf16, kTB)
 
-static const PlainEntry kPlain = JAC_PLAIN(BF16, 2, 8, 0);
+static const PlainEntry kPlain = JAC_PLAIN(BF16, 4, 8, 0);
 const PlainEntry* plain_entry_bf16() { return &kPlain; }
 
 }  // namespace jac

@@ -11,7 +11,7 @@ static const TBEntry kTB[] = {
 };
 JAC_TABLE(tb_entries_f32, kTB)
 
-static const PlainEntry kPlain = JAC_PLAIN(F32, 1, 8, 0);
+static const PlainEntry kPlain = JAC_PLAIN(F32, 4, 8, 0);
 const PlainEntry* plain_entry_f32() { return &kPlain; }
 
 }  // namespace jac

@@ -40,18 +40,18 @@ ALGO_BYTES_PER_LUP = {"f64": 16, "f32": 8, "bf16": 4}
 # figure scales the 384^3 capture by the lattice-site updates (traffic is
 # proportional to them: 16 B per update, no re-reads).
 TRAFFIC_PER_LAUNCH = {
-    # profiles/plain_sweep_f64_emu5_384cubed.md: 477.6 MB read + 412.8 MB written
+    # profiles/plain_sweep_f64_emu6_384cubed.md: 480.1 MB read + 408.8 MB written
     # for 384^3 (56.6 M updates) -> x (512/384)^3
-    "plain_sweep_kernel<F64,emu=5>": round((477572352 + 412830976) * (512 / 384) ** 3),
+    "plain_sweep_kernel<F64,emu=6>": round((480093696 + 408763904) * (512 / 384) ** 3),
 }
 
-# Pipe cost of the FP64 plain sweep with 2.5 of its 5 additions on the integer
-# pipes (profiles/plain_sweep_f64_emu5_384cubed.md): FP64 pipe 3.5 ops per update
-# at 2 ops/clk/SM = 1.75 SM-cycles per update; the integer ALU pipe is busy 1.81
-# SM-cycles per update (ncu sm__pipe_alu_cycles_active, 74.8 % of 898.8 k cycles
-# per SMSP for 93.1 k updates per SMSP, 4 SMSPs per SM).  The binding pipe sets
-# the ceiling: SMs x clock / max(1.75, 1.81).
-F64_EMU_SM_CYCLES_PER_LUP = {"fp64": 1.75, "alu": 1.806}
+# Pipe cost of the FP64 plain sweep with 3 of its 5 additions on the integer
+# pipes (profiles/plain_sweep_f64_emu6_384cubed.md): FP64 pipe 3 ops per update at
+# 2 ops/clk/SM = 1.50 SM-cycles per update; the integer ALU pipe is busy 1.885
+# SM-cycles per update (ncu sm__pipe_alu_cycles_active 92.3 % of 761.1 k active
+# cycles per SMSP, 384^3 updates over 608 SMSPs, 4 SMSPs per SM).  The binding
+# pipe sets the ceiling: SMs x clock / max(1.50, 1.885).
+F64_EMU_SM_CYCLES_PER_LUP = {"fp64": 1.50, "alu": 1.885}
 
 
 def parse():
@@ -473,12 +473,12 @@ def run_ours(args):
         lups_launch = NX * NY * NZ * sweeps_per_launch
         achieved_glups = lups_launch / launch_s / 1e9
         fp64_only = DP_OPS_PER_CLK_PER_SM * SM_COUNT * mhz * 1e6 / DP_OPS_PER_LUP / 1e9
-        if emu == 5:
+        if emu == 6:
             cyc = max(F64_EMU_SM_CYCLES_PER_LUP.values())
             peak_glups = SM_COUNT * mhz * 1e6 / cyc / 1e9
-            src = ("two-pipe ceiling: 152 SMs x %.0f MHz / max(FP64 pipe 1.75, integer ALU pipe "
-                   "1.81) SM-cycles per update (FP64 unit 2 ops/clk/SM; ALU cycles from ncu, "
-                   "profiles/plain_sweep_f64_emu5_384cubed.md)" % mhz)
+            src = ("two-pipe ceiling: 152 SMs x %.0f MHz / max(FP64 pipe 1.50, integer ALU pipe "
+                   "1.885) SM-cycles per update (FP64 unit 2 ops/clk/SM; ALU cycles from ncu, "
+                   "profiles/plain_sweep_f64_emu6_384cubed.md)" % mhz)
         else:
             peak_glups = fp64_only
             src = ("FP64 pipe: %d DP ops/clk/SM x %d SMs x %.0f MHz / 6 ops per update"

@@ -18,7 +18,7 @@
 using namespace jac;
 
 namespace {
-constexpr int kDefaultF64Emu = 5;  // half additions per plane (2.5 of 5)
+constexpr int kDefaultF64Emu = 6;  // half additions per plane (3 of 5)
 }
 
 struct jacobi_s {
@@ -189,7 +189,9 @@ TBGeom tb_geom(const jacobi_s* h, const TBEntry& e) {
 }
 
 int plain_chunks(const jacobi_s* h, const PlainEntry* pe, dim3* grid, int* kchunk) {
-    const int nvec = (pe->V == 1) ? h->g.nx : h->g.nx / pe->V + 1;
+    // interior-aligned kernels (V == 1, or FP64) start at x = 1; vector kernels at 0
+    const bool aligned_x1 = pe->V == 1 || h->dtype == JAC_F64;
+    const int nvec = aligned_x1 ? (h->g.nx + pe->V - 1) / pe->V : h->g.nx / pe->V + 1;
     grid->x = (nvec + 31) / 32;
     grid->y = (h->g.ny + pe->WY - 1) / pe->WY;
     int occ = 1;

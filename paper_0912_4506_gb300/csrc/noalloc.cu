@@ -173,7 +173,8 @@ extern "C" int jacobi_sweep_noalloc(int nx, int ny, int nz, int dtype, void* gri
         const PlainEntry* pe = dtype == JAC_F64   ? plain_entry_f64()
                                : dtype == JAC_F32 ? plain_entry_f32()
                                                   : plain_entry_bf16();
-        const int nvec = (pe->V == 1) ? nx : nx / pe->V + 1;
+        const bool aligned_x1 = pe->V == 1 || dtype == JAC_F64;
+        const int nvec = aligned_x1 ? (nx + pe->V - 1) / pe->V : nx / pe->V + 1;
         dim3 grid3((nvec + 31) / 32, (ny + pe->WY - 1) / pe->WY, 1);
         int kchunk = nz;
         for (int s = 0; s < nsweeps; ++s) {

@@ -130,9 +130,12 @@ __device__ __forceinline__ void plain_march(const typename Tr::S* __restrict__ A
     if (k <= k1) plane_step(k, kEven);
 }
 
-// FP64 variant of the march: loads one plane ahead only.  The FP64 sweep is
-// bound by its arithmetic pipes, not by memory latency, and the shallower
-// pipeline keeps the register count (and so the occupancy) lower.
+// FP64 variant of the march.  The FP64 sweep is bound by its arithmetic pipes
+// (the FP64 unit and, for the emulated additions, the integer ALU), so this
+// march saves instructions rather than latency: cells are interior-aligned
+// (x0 = 1 + V*lane, no idle lanes at the row end), loaded as scalars, the pointers
+// advance by one plane per step instead of being recomputed, and each plane is
+// loaded one step ahead only (fewer registers, more resident warps).
 template <class Tr, int V, int NEMU>
 __device__ __forceinline__ void plain_march_shallow(const typename Tr::S* __restrict__ A,
                                             typename Tr::S* __restrict__ B, const Geom& g,
@@ -140,7 +143,6 @@ __device__ __forceinline__ void plain_march_shallow(const typename Tr::S* __rest
                                             bool loadable, const bool (&interior)[V],
                                             bool all_interior, bool left_ok, bool right_ok,
                                             long long row) {
-    using S = typename Tr::S;
     using C = typename Tr::C;
     const unsigned FULL = 0xffffffffu;
     const C c6 = Tr::sixth();
@@ -150,54 +152,60 @@ __device__ __forceinline__ void plain_march_shallow(const typename Tr::S* __rest
         }
         return Tr::add(a, b);
     };
+    // per cell: inside the row allocation (the cell past nx is the boundary value
+    // that the neighbouring lane needs, so a partly outside vector still loads)
+    bool okl[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) okl[e] = (x0 + e) < g.px;
+    auto load = [&](const typename Tr::S* p, C (&out)[V]) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) out[e] = okl[e] ? Tr::ld(__ldg(p + e)) : C(0);
+    };
 
+    const long long plane = g.plane, px = g.px;
+    const typename Tr::S* pa = A + row + plane * k0;  // (x0, y, k) of A
+    typename Tr::S* pb = B + row + plane * k0;        // (x0, y, k) of B
     C dn[V], ct[V], up[V], no[V], so[V];
-    load_vec<Tr, V>(A + row + g.plane * (k0 - 1), loadable, dn);
-    load_vec<Tr, V>(A + row + g.plane * k0, loadable, ct);
+    load(pa - plane, dn);
+    load(pa, ct);
 
-    auto plane_step = [&](int k, int nemu) {
-        const long long base = row + g.plane * k;
-        load_vec<Tr, V>(A + base + g.plane, loadable, up);
-        load_vec<Tr, V>(A + base - g.px, loadable, no);
-        load_vec<Tr, V>(A + base + g.px, loadable, so);
+    auto plane_step = [&](int nemu) {
+        load(pa + plane, up);
+        load(pa - px, no);
+        load(pa + px, so);
         C left = __shfl_up_sync(FULL, ct[V - 1], 1);
         C right = __shfl_down_sync(FULL, ct[0], 1);
-        if (lane == 0) left = left_ok ? Tr::ld(__ldg(A + base - 1)) : C(0);
-        if (lane == 31) right = right_ok ? Tr::ld(__ldg(A + base + V)) : C(0);
-
-        Vec<S, V> outv;
+        if (lane == 0) left = left_ok ? Tr::ld(__ldg(pa - 1)) : C(0);
+        if (lane == 31) right = right_ok ? Tr::ld(__ldg(pa + V)) : C(0);
 #pragma unroll
         for (int e = 0; e < V; ++e) {
             const C l = (e == 0) ? left : ct[e - 1];
             const C r = (e == V - 1) ? right : ct[e + 1];
-            C s = add(0, nemu, l, r);
-            s = add(1, nemu, s, no[e]);
-            s = add(2, nemu, s, so[e]);
-            s = add(3, nemu, s, dn[e]);
-            s = add(4, nemu, s, up[e]);
-            outv.v[e] = Tr::st(Tr::mul(s, c6));
-        }
-        if (all_interior) {
-            *reinterpret_cast<Vec<S, V>*>(B + base) = outv;
-        } else {
-#pragma unroll
-            for (int e = 0; e < V; ++e)
-                if (interior[e]) B[base + e] = outv.v[e];
+            C sum = add(0, nemu, l, r);
+            sum = add(1, nemu, sum, no[e]);
+            sum = add(2, nemu, sum, so[e]);
+            sum = add(3, nemu, sum, dn[e]);
+            sum = add(4, nemu, sum, up[e]);
+            if (interior[e]) pb[e] = Tr::st(Tr::mul(sum, c6));
         }
 #pragma unroll
         for (int e = 0; e < V; ++e) {
             dn[e] = ct[e];
             ct[e] = up[e];
         }
+        pa += plane;
+        pb += plane;
     };
     constexpr int kEven = NEMU / 2, kOdd = (NEMU + 1) / 2;
     int k = k0;
 #pragma unroll 1
     for (; k + 1 <= k1; k += 2) {
-        plane_step(k, kEven);
-        plane_step(k + 1, kOdd);
+        plane_step(kEven);
+        plane_step(kOdd);
     }
-    if (k <= k1) plane_step(k, kEven);
+    if (k <= k1) plane_step(kEven);
+    (void)all_interior;
+    (void)loadable;
 }
 
 // `fast` (FP64, NEMU > 0): device flag written by range_check_kernel; when it is
@@ -208,7 +216,8 @@ template <class Tr, int V, int WY, int NEMU>
 __global__ void __launch_bounds__(32 * WY)
     plain_sweep_kernel(const typename Tr::S* __restrict__ A, typename Tr::S* __restrict__ B,
                        const Geom g, const int kchunk, const int* __restrict__ fast) {
-    constexpr int XOFF = (V == 1) ? 1 : 0;
+    // FP64 and V == 1: interior-aligned cells (scalar loads); else 16-byte vectors
+    constexpr int XOFF = (V == 1 || sizeof(typename Tr::S) == 8) ? 1 : 0;
     const int lane = threadIdx.x;
     const int x0 = XOFF + (int)(blockIdx.x * 32 + lane) * V;
     const int y = 1 + (int)(blockIdx.y * WY + threadIdx.y);
@@ -229,7 +238,7 @@ __global__ void __launch_bounds__(32 * WY)
     }
     const bool left_ok = (x0 >= 1);
     const bool right_ok = (x0 + V) < g.px;
-    const long long row = g.lin(loadable ? x0 : 0, y, 0);
+    const long long row = g.lin(x0 < g.px ? x0 : 0, y, 0);
 
     if constexpr (sizeof(typename Tr::S) == 8) {
         if (NEMU > 0 && fast != nullptr && *fast)

@@ -13,10 +13,10 @@ JAC_TABLE(tb_entries_f64, kTB)
 
 // plain sweeps with 0..4 of the additions on the integer pipes, in half
 // additions per plane (see plain_march); entry 0 is the all-FP64-unit kernel
-static const PlainEntry kPlain[] = {JAC_PLAIN(F64, 1, 8, 0), JAC_PLAIN(F64, 1, 8, 2),
-                                    JAC_PLAIN(F64, 1, 8, 4), JAC_PLAIN(F64, 1, 8, 5),
-                                    JAC_PLAIN(F64, 1, 8, 6), JAC_PLAIN(F64, 1, 8, 7),
-                                    JAC_PLAIN(F64, 1, 8, 8)};
+static const PlainEntry kPlain[] = {JAC_PLAIN(F64, 2, 8, 0), JAC_PLAIN(F64, 2, 8, 2),
+                                    JAC_PLAIN(F64, 2, 8, 4), JAC_PLAIN(F64, 2, 8, 5),
+                                    JAC_PLAIN(F64, 2, 8, 6), JAC_PLAIN(F64, 2, 8, 7),
+                                    JAC_PLAIN(F64, 2, 8, 8)};
 const PlainEntry* plain_entries_f64(int* n) {
     *n = (int)(sizeof(kPlain) / sizeof(kPlain[0]));
     return kPlain;

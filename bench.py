@@ -40,18 +40,18 @@ ALGO_BYTES_PER_LUP = {"f64": 16, "f32": 8, "bf16": 4}
 # figure scales the 384^3 capture by the lattice-site updates (traffic is
 # proportional to them: 16 B per update, no re-reads).
 TRAFFIC_PER_LAUNCH = {
-    # profiles/plain_sweep_f64_emu6_384cubed.md: 480.1 MB read + 408.8 MB written
+    # profiles/plain_sweep_f64_emu6_384cubed.md: 487.9 MB read + 409.7 MB written
     # for 384^3 (56.6 M updates) -> x (512/384)^3
-    "plain_sweep_kernel<F64,emu=6>": round((480093696 + 408763904) * (512 / 384) ** 3),
+    "plain_sweep_kernel<F64,emu=6>": round((487892736 + 409680896) * (512 / 384) ** 3),
 }
 
 # Pipe cost of the FP64 plain sweep with 3 of its 5 additions on the integer
 # pipes (profiles/plain_sweep_f64_emu6_384cubed.md): FP64 pipe 3 ops per update at
-# 2 ops/clk/SM = 1.50 SM-cycles per update; the integer ALU pipe is busy 1.885
-# SM-cycles per update (ncu sm__pipe_alu_cycles_active 92.3 % of 761.1 k active
+# 2 ops/clk/SM = 1.50 SM-cycles per update; the integer ALU pipe is busy 1.61
+# SM-cycles per update (ncu sm__pipe_alu_cycles_active 85.0 % of 706.9 k active
 # cycles per SMSP, 384^3 updates over 608 SMSPs, 4 SMSPs per SM).  The binding
-# pipe sets the ceiling: SMs x clock / max(1.50, 1.885).
-F64_EMU_SM_CYCLES_PER_LUP = {"fp64": 1.50, "alu": 1.885}
+# pipe sets the ceiling: SMs x clock / max(1.50, 1.61).
+F64_EMU_SM_CYCLES_PER_LUP = {"fp64": 1.497, "alu": 1.613}
 
 
 def parse():
@@ -477,7 +477,7 @@ def run_ours(args):
             cyc = max(F64_EMU_SM_CYCLES_PER_LUP.values())
             peak_glups = SM_COUNT * mhz * 1e6 / cyc / 1e9
             src = ("two-pipe ceiling: 152 SMs x %.0f MHz / max(FP64 pipe 1.50, integer ALU pipe "
-                   "1.885) SM-cycles per update (FP64 unit 2 ops/clk/SM; ALU cycles from ncu, "
+                   "1.61) SM-cycles per update (FP64 unit 2 ops/clk/SM; ALU cycles from ncu, "
                    "profiles/plain_sweep_f64_emu6_384cubed.md)" % mhz)
         else:
             peak_glups = fp64_only

@@ -37,6 +37,64 @@ __device__ __forceinline__ uint32_t shl32(uint32_t x, uint32_t n) {  // n in [0,
 // time is exactly what the integer path is meant to save.
 static __device__ __noinline__ double add_fp64_unit(double a, double b) { return __dadd_rn(a, b); }
 
+// Integer additions on the FMA pipe: a*one + b with `one` a runtime 1 (a kernel
+// argument, so the compiler cannot fold it into an ALU add).  The sweep is bound
+// by the integer ALU pipe while the FMA pipe idles, so these move work across.
+__device__ __forceinline__ uint32_t add_f(uint32_t a, uint32_t b, uint32_t one) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(one), "r"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long add64_f(unsigned long long a, unsigned long long b,
+                                                      uint32_t one) {
+    uint32_t lo, hi;
+    asm("mad.lo.cc.u32 %0, %2, %4, %3;\n\tmadc.lo.u32 %1, %5, %4, %6;"
+        : "=r"(lo), "=r"(hi)
+        : "r"((uint32_t)a), "r"((uint32_t)b), "r"(one), "r"((uint32_t)(a >> 32)),
+          "r"((uint32_t)(b >> 32)));
+    return ((unsigned long long)hi << 32) | lo;
+}
+
+// As add_pos_exact below, with its additions issued to the FMA pipe (a*one + b,
+// a*m1 + b with m1 = -one, a*p20 + b with p20 = one << 20, all runtime values).
+__device__ __forceinline__ uint32_t mad_u(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t r;
+    asm("mad.lo.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(b), "r"(c));
+    return r;
+}
+
+__device__ __forceinline__ double add_pos_exact_f(double a, double b, uint32_t one) {
+    const uint32_t m1 = 0u - one, p20 = one << 20;  // hoisted out of the loops
+    const unsigned long long A = (unsigned long long)__double_as_longlong(a);
+    const unsigned long long B = (unsigned long long)__double_as_longlong(b);
+    const bool swap = (uint32_t)(A >> 32) < (uint32_t)(B >> 32);
+    const unsigned long long X = swap ? B : A;
+    const unsigned long long Y = swap ? A : B;
+    const uint32_t ex = (uint32_t)(X >> 52);
+    const uint32_t d = mad_u((uint32_t)(Y >> 52), m1, ex);     // ex - ey
+    const uint32_t dd = d > 31u ? 31u : d;
+    const unsigned long long kMant = 0x000FFFFFFFFFFFFFull, kHidden = 0x0010000000000000ull;
+    const unsigned long long mx = (X & kMant) | kHidden;
+    const unsigned long long my = (Y & kMant) | kHidden;
+    const uint32_t F = shl32((uint32_t)my, mad_u(dd, m1, 32u));  // 32 - dd
+    const unsigned long long S = add64_f(mx, my >> dd, one);
+    const uint32_t c = (uint32_t)(S >> 53);
+    const unsigned long long Sn = S >> c;
+    const uint32_t Fc = c ? (((uint32_t)S << 31) | (F >> 1) | (F & 1u)) : F;
+    const uint32_t up =
+        (uint32_t)(add64_f((unsigned long long)Fc, 0x7FFFFFFFull + (Sn & 1ull), one) >> 32);
+    const unsigned long long M = add64_f(Sn, (unsigned long long)up, one);
+    // biased exponent (ex + c - 1) placed at bit 52 and added to M (no carry into
+    // the low word: the shifted exponent has none)
+    const uint32_t e1 = mad_u(ex, one, mad_u(c, one, 0xFFFFFFFFu));
+    const uint32_t rhi = mad_u(e1, p20, (uint32_t)(M >> 32));
+    double r = __longlong_as_double((long long)(((unsigned long long)rhi << 32) | (uint32_t)M));
+    if (__any_sync(__activemask(), d > 31u)) {
+        if (d > 31u) r = add_fp64_unit(a, b);
+    }
+    return r;
+}
+
 __device__ __forceinline__ double add_pos_exact(double a, double b) {
     const unsigned long long A = (unsigned long long)__double_as_longlong(a);
     const unsigned long long B = (unsigned long long)__double_as_longlong(b);

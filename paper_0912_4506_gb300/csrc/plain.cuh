@@ -142,13 +142,13 @@ __device__ __forceinline__ void plain_march_shallow(const typename Tr::S* __rest
                                             int k0, int k1, int x0, int y, int lane,
                                             bool loadable, const bool (&interior)[V],
                                             bool all_interior, bool left_ok, bool right_ok,
-                                            long long row) {
+                                            long long row, uint32_t one) {
     using C = typename Tr::C;
     const unsigned FULL = 0xffffffffu;
     const C c6 = Tr::sixth();
-    auto add = [](int idx, int nemu, C a, C b) -> C {
+    auto add = [one](int idx, int nemu, C a, C b) -> C {
         if constexpr (NEMU > 0) {
-            if (idx < nemu) return add_pos_exact(a, b);
+            if (idx < nemu) return add_pos_exact_f(a, b, one);
         }
         return Tr::add(a, b);
     };
@@ -215,7 +215,8 @@ __device__ __forceinline__ void plain_march_shallow(const typename Tr::S* __rest
 template <class Tr, int V, int WY, int NEMU>
 __global__ void __launch_bounds__(32 * WY)
     plain_sweep_kernel(const typename Tr::S* __restrict__ A, typename Tr::S* __restrict__ B,
-                       const Geom g, const int kchunk, const int* __restrict__ fast) {
+                       const Geom g, const int kchunk, const int* __restrict__ fast,
+                       const uint32_t one) {
     // FP64 and V == 1: interior-aligned cells (scalar loads); else 16-byte vectors
     constexpr int XOFF = (V == 1 || sizeof(typename Tr::S) == 8) ? 1 : 0;
     const int lane = threadIdx.x;
@@ -243,10 +244,10 @@ __global__ void __launch_bounds__(32 * WY)
     if constexpr (sizeof(typename Tr::S) == 8) {
         if (NEMU > 0 && fast != nullptr && *fast)
             plain_march_shallow<Tr, V, NEMU>(A, B, g, k0, k1, x0, y, lane, loadable, interior,
-                                             all_interior, left_ok, right_ok, row);
+                                             all_interior, left_ok, right_ok, row, one);
         else
             plain_march_shallow<Tr, V, 0>(A, B, g, k0, k1, x0, y, lane, loadable, interior,
-                                          all_interior, left_ok, right_ok, row);
+                                          all_interior, left_ok, right_ok, row, one);
     } else {
         plain_march<Tr, V, 0>(A, B, g, k0, k1, x0, y, lane, loadable, interior, all_interior,
                               left_ok, right_ok, row);

@@ -19,7 +19,7 @@ cudaError_t plain_launch(const void* A, void* B, const Geom& g, int kchunk, dim3
                          const int* fast, cudaStream_t st) {
     using S = typename TR::S;
     plain_sweep_kernel<TR, V, WY, NEMU><<<grid, dim3(32, WY), 0, st>>>(
-        static_cast<const S*>(A), static_cast<S*>(B), g, kchunk, fast);
+        static_cast<const S*>(A), static_cast<S*>(B), g, kchunk, fast, 1u);
     return cudaGetLastError();
 }
 

@@ -396,6 +396,42 @@ def variant_adjoint(dev, n=256, nsweeps=50, t=4):
     return rows
 
 
+def variant_slabs(dev, n=512, nslabs=4, h=4, nsweeps=100):
+    """z-slab decomposition with multi-layer halos (one GPU): 512^3 FP32 in 4 slabs,
+    4-plane halos exchanged every 4 sweeps, beside the single-grid blocked sweep."""
+    import torch
+    from paper_0912_4506_gb300 import api, inputs, slabs
+    a = inputs.to_dtype(inputs.uniform_grid_f64(n, n, n, px=inputs.row_pitch(n, "f32")), "f32")
+    A = api.from_numpy(a, n, dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    sj = slabs.SlabJacobi(A, nslabs, h)
+    sj.sweep(h)
+    torch.cuda.synchronize()
+    ev[0].record()
+    sj.sweep(nsweeps)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms_slab = ev[0].elapsed_time(ev[1])
+    sj.close()
+    j = api.Jacobi(A)
+    j.sweep(h, h)
+    torch.cuda.synchronize()
+    ev[0].record()
+    j.sweep(nsweeps, h)
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms_one = ev[0].elapsed_time(ev[1])
+    j.close()
+    del A, sj, j
+    torch.cuda.empty_cache()
+    lups = n ** 3 * nsweeps
+    return {"slabs_glups": round(lups / ms_slab / 1e6, 2),
+            "single_grid_glups": round(lups / ms_one / 1e6, 2),
+            "config": {"n": n, "dtype": "f32", "slabs": nslabs, "halo": h, "t": h,
+                       "sweeps": nsweeps,
+                       "exchange": "h+1 planes per side every h sweeps (device copies)"}}
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_setup()
@@ -525,6 +561,7 @@ def run_ours(args):
         line["precision_1024"] = variant_precision(dev)
         line["batched_64"] = variant_batched(dev)
         line["adjoint_256"] = variant_adjoint(dev)
+        line["slabs_512"] = variant_slabs(dev)
     if world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(a64)
         line["cpu_baseline"] = {"value": round(rate, 4), "unit": "GLUP/s", "cores": cores,

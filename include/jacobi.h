@@ -270,6 +270,17 @@ JAC_API int jacobi_sweep_noalloc(int nx, int ny, int nz, int dtype, void *grid,
 JAC_API int jacobi_emulated_add(const double *a, const double *b, double *out, long long n,
                                 void *stream);
 
+/*
+ * jacobi_copy_planes — copy nplanes consecutive k-planes of one padded grid into
+ * another of the same row pitch and ny (plane size plane_elems = row_pitch*(ny+2)
+ * elements of elem_bytes each): the halo exchange of the z-slab decomposition
+ * (multi-layer halos, Sect. 2.1).  dst/src point at the first plane to copy;
+ * device memory; asynchronous on `stream`.  Planes of one slab grid must not
+ * overlap the copied range of another.
+ */
+JAC_API int jacobi_copy_planes(void *dst, const void *src, long long plane_elems,
+                               int elem_bytes, int nplanes, void *stream);
+
 /* jacobi_check — wait for the handle's stream and report a device-side status
  * (JAC_ETIMEOUT when a bounded wait ran out) or a CUDA error (JAC_ECUDA).  The
  * status word is cleared. */

@@ -17,7 +17,7 @@ EXPORTS = ["jacobi_create", "jacobi_sweep", "jacobi_sweep_ex", "jacobi_plan",
            "jacobi_upload", "jacobi_download", "jacobi_check", "jacobi_destroy",
            "jacobi_strerror", "jacobi_version", "jacobi_sweep_noalloc",
            "jacobi_batch_create", "jacobi_batch_run", "jacobi_batch_info", "jacobi_batch_check",
-           "jacobi_batch_destroy", "jacobi_emulated_add"]
+           "jacobi_batch_destroy", "jacobi_emulated_add", "jacobi_copy_planes"]
 
 JAC_BATCH_NO_GRAPH, JAC_BATCH_TEST_MISSING_PRODUCER = 1, 2
 
@@ -74,6 +74,7 @@ def load(path=None):
         "jacobi_batch_check": ([P], I),
         "jacobi_batch_destroy": ([P], I),
         "jacobi_emulated_add": ([P, P, P, LL, P], I),
+        "jacobi_copy_planes": ([P, P, LL, I, I, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -209,3 +210,8 @@ def jacobi_batch_destroy(h):
 
 def jacobi_emulated_add(a_ptr, b_ptr, out_ptr, n, stream):
     _ck(load().jacobi_emulated_add(a_ptr, b_ptr, out_ptr, n, stream), "jacobi_emulated_add")
+
+
+def jacobi_copy_planes(dst_ptr, src_ptr, plane_elems, elem_bytes, nplanes, stream):
+    _ck(load().jacobi_copy_planes(dst_ptr, src_ptr, plane_elems, elem_bytes, nplanes, stream),
+        "jacobi_copy_planes")

@@ -467,6 +467,19 @@ int jacobi_download(jacobi_t h, void* host, int from_b) {
     return JAC_OK;
 }
 
+int jacobi_copy_planes(void* dst, const void* src, long long plane_elems, int elem_bytes,
+                       int nplanes, void* stream) {
+    if (!dst || !src || plane_elems < 1 || nplanes < 0 ||
+        (elem_bytes != 2 && elem_bytes != 4 && elem_bytes != 8))
+        return JAC_EINVAL;
+    if (nplanes == 0) return JAC_OK;
+    const size_t bytes = (size_t)plane_elems * (size_t)elem_bytes * (size_t)nplanes;
+    return cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice,
+                           static_cast<cudaStream_t>(stream)) == cudaSuccess
+               ? JAC_OK
+               : JAC_ECUDA;
+}
+
 int jacobi_check(jacobi_t h) {
     if (!h) return JAC_EINVAL;
     if (cudaSetDevice(h->device) != cudaSuccess) return JAC_ECUDA;

@@ -333,10 +333,12 @@ def variant_batched(dev):
             "depth_histogram": hist, "launches_per_run": 1}
 
 
-def variant_adjoint(dev, n=256, nsweeps=50, t=4):
+def variant_adjoint(dev, n=256, nsweeps=50, t_fwd=2, t_adj=(("f32", 3), ("f64", 1))):
     """256^3 FP32, 50 sweeps: forward (blocked), adjoint (blocked, with the boundary
     gradient), beside the plain FP32 sweep; error of the FP32 gradient against the
-    FP64 adjoint of the same loss."""
+    FP64 adjoint of the same loss.  Depths: the fastest measured on GB300 for each
+    kind (the library's defaults)."""
+    t_adj = dict(t_adj)
     import torch
     from paper_0912_4506_gb300 import api, inputs
     x = inputs.uniform_grid_f64(n, n, n)
@@ -362,11 +364,12 @@ def variant_adjoint(dev, n=256, nsweeps=50, t=4):
         j = api.Jacobi(xg)
         if dtype == "f32":
             ms_plain = timed(lambda: j.sweep(nsweeps, 1))
-            ms_fwd = timed(lambda: j.sweep(nsweeps, t))
+            ms_fwd = timed(lambda: j.sweep(nsweeps, t_fwd))
         lam = api.alloc_like(Wg)
         gb = api.alloc_like(Wg)
         jl = api.Jacobi(lam)
         # timing: repeated adjoint calls continue the iteration (same work per call)
+        t = t_adj[dtype]
         ms_adj = timed(lambda: jl.adjoint(gb, nsweeps, t))
         # the gradient itself: lambda_n = W on the interior, grad_g starts at W's
         # boundary layer (the direct term)
@@ -391,7 +394,8 @@ def variant_adjoint(dev, n=256, nsweeps=50, t=4):
     err = float((grads["f32"] - grads["f64"]).abs().max())
     rows["grad_max_abs_err_f32_vs_f64"] = err
     rows["grad_max_rel_err_f32_vs_f64"] = err / float(grads["f64"].abs().max())
-    rows["config"] = {"n": n, "sweeps": nsweeps, "t": t, "loss": "sum(W * A_n), W ~ N(0,1) seed 3"}
+    rows["config"] = {"n": n, "sweeps": nsweeps, "t_fwd": t_fwd, "t_adjoint": t_adj,
+                      "loss": "sum(W * A_n), W ~ N(0,1) seed 3"}
     torch.cuda.empty_cache()
     return rows
 

@@ -48,10 +48,11 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 template <class Tr, int T>
 __device__ __forceinline__ void batch_tile(const CUtensorMap* map, const TBArgs& a, int bx,
                                            int by, int bz, unsigned char* smem, int* s_abort) {
-    if (tile_inside_xy<kBatchV, kBatchNW, T>(a, bx, by))
-        tb_tile<Tr, kBatchV, kBatchNW, T, MODE_PLAIN, true>(map, a, bx, by, bz, smem, s_abort);
+    if (tile_inside_xy<kBatchV, kBatchNW, 1, T>(a, bx, by))
+        tb_tile<Tr, kBatchV, kBatchNW, 1, T, MODE_PLAIN, true>(map, a, bx, by, bz, smem, s_abort);
     else
-        tb_tile<Tr, kBatchV, kBatchNW, T, MODE_PLAIN, false>(map, a, bx, by, bz, smem, s_abort);
+        tb_tile<Tr, kBatchV, kBatchNW, 1, T, MODE_PLAIN, false>(map, a, bx, by, bz, smem,
+                                                                s_abort);
 }
 
 template <class Tr>

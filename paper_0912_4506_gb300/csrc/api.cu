@@ -34,6 +34,9 @@ struct jacobi_s {
     CUtensorMap map_a;    // TMA descriptors of A and B (box set per entry shape)
     CUtensorMap map_b;
     int map_box_x, map_box_y;
+    CUtensorMap map_rho;  // right-hand side of the correction sweeps (last rho seen)
+    const void* rho_ptr;
+    int rho_box_x, rho_box_y;
 };
 
 namespace {
@@ -397,8 +400,18 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         args.x0_first = gm.x0_first;
         args.kz = gm.kz;
         args.status = h->status;
+        if (mode == MODE_RHS &&
+            (rho != h->rho_ptr || EX != h->rho_box_x || EY != h->rho_box_y)) {
+            if (make_map(&h->map_rho, h, const_cast<void*>(rho), EX, EY) != JAC_OK)
+                return JAC_ECUDA;
+            h->rho_ptr = rho;
+            h->rho_box_x = EX;
+            h->rho_box_y = EY;
+        }
         const CUtensorMap& map = cur_b ? h->map_b : h->map_a;
-        if (e->launch(map, args, dim3(gm.ntx, gm.nty, gm.nchunk), h->stream) != cudaSuccess)
+        const CUtensorMap& map_rho = mode == MODE_RHS ? h->map_rho : map;
+        if (e->launch(map, map_rho, args, dim3(gm.ntx, gm.nty, gm.nchunk), h->stream) !=
+            cudaSuccess)
             return JAC_ECUDA;
         cur_b ^= 1;
     }

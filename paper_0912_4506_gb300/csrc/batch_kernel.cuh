@@ -49,9 +49,10 @@ template <class Tr, int T>
 __device__ __forceinline__ void batch_tile(const CUtensorMap* map, const TBArgs& a, int bx,
                                            int by, int bz, unsigned char* smem, int* s_abort) {
     if (tile_inside_xy<kBatchV, kBatchNW, 1, T>(a, bx, by))
-        tb_tile<Tr, kBatchV, kBatchNW, 1, T, MODE_PLAIN, true>(map, a, bx, by, bz, smem, s_abort);
+        tb_tile<Tr, kBatchV, kBatchNW, 1, T, MODE_PLAIN, true>(map, nullptr, a, bx, by, bz, smem,
+                                                               s_abort);
     else
-        tb_tile<Tr, kBatchV, kBatchNW, 1, T, MODE_PLAIN, false>(map, a, bx, by, bz, smem,
+        tb_tile<Tr, kBatchV, kBatchNW, 1, T, MODE_PLAIN, false>(map, nullptr, a, bx, by, bz, smem,
                                                                 s_abort);
 }
 

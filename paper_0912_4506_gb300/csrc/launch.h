@@ -12,8 +12,10 @@ namespace jac {
 
 struct TBArgs;
 
-using TBLaunchFn = cudaError_t (*)(const CUtensorMap& map, const TBArgs& a, dim3 grid,
-                                   cudaStream_t st);
+// map: the grid read by the pass; map_rho: the right-hand side (correction
+// sweeps; any valid map otherwise)
+using TBLaunchFn = cudaError_t (*)(const CUtensorMap& map, const CUtensorMap& map_rho,
+                                   const TBArgs& a, dim3 grid, cudaStream_t st);
 
 // One instantiation of the temporally-blocked kernel.
 struct TBEntry {

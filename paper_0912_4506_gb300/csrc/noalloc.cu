@@ -211,8 +211,8 @@ extern "C" int jacobi_sweep_noalloc(int nx, int ny, int nz, int dtype, void* gri
             a.x0_first = p.x0_first;
             a.kz = p.kz;
             a.status = status;
-            if (p.e->launch(cur_other ? map_other : map_grid, a, dim3(p.ntx, p.nty, p.nchunk),
-                            st) != cudaSuccess)
+            const CUtensorMap& m = cur_other ? map_other : map_grid;
+            if (p.e->launch(m, m, a, dim3(p.ntx, p.nty, p.nchunk), st) != cudaSuccess)
                 return JAC_ECUDA;
             cur_other ^= 1;
             left -= d;

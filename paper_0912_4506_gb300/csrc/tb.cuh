@@ -62,7 +62,7 @@ struct TBArgs {
     int* status;        // device status word (timeouts)
 };
 
-template <int V, int NW, int R, int T, int NS, class S>
+template <int V, int NW, int R, int T, int NS, class S, int NSR = 0>
 struct TBLayout {
     static constexpr int EX = 32 * V;
     static constexpr int EY = NW * R;                 // rows of the extended tile
@@ -73,14 +73,24 @@ struct TBLayout {
     // mbarriers at the start; the header's last row-sized stretch and one row
     // after the level buffers are guard rows, so that the rows just above and
     // below the extended tile can be read without clamping (their values only
-    // reach cells outside the valid region of the level being computed)
+    // reach cells outside the valid region of the level being computed).  The
+    // NSR slots of the right-hand-side ring (correction sweeps) follow.
     static constexpr int HEADER = 1024;
     static_assert(EX * sizeof(S) + 64 <= HEADER, "guard row overlaps the mbarriers");
-    static constexpr size_t bytes() {
-        return HEADER + (size_t)NS * PLANE * sizeof(S) + (size_t)NLB * LPLANE * sizeof(S) +
-               (size_t)EX * sizeof(S);
-    }
+    static constexpr size_t RHO_OFF =
+        HEADER + (size_t)NS * PLANE * sizeof(S) + (size_t)NLB * LPLANE * sizeof(S) +
+        (size_t)EX * sizeof(S);
+    static_assert(RHO_OFF % 128 == 0, "TMA destinations must stay 128-byte aligned");
+    static constexpr size_t bytes() { return RHO_OFF + (size_t)NSR * PLANE * sizeof(S); }
 };
+
+// Slots of the right-hand-side ring for depth T: a plane is issued together with
+// the grid plane of the same k, NS-1 steps before its first use, and is read by
+// the levels 1..T, so NS + T slots keep every plane until its last reader is done.
+template <int MODE, int NS, int T>
+constexpr int rho_slots() {
+    return MODE == MODE_RHS ? NS + T : 0;
+}
 
 template <int N>
 using IC = std::integral_constant<int, N>;
@@ -95,19 +105,24 @@ using IC = std::integral_constant<int, N>;
 // row), so a level costs two shared-memory row reads and at most two row writes
 // per R*V cells.
 template <class Tr, int V, int NW, int R, int T, int MODE, bool FAST>
-__device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a, int bx,
-                                        int by, int bz, unsigned char* smem, int* s_abort) {
+__device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorMap* tmap_rho,
+                                        const TBArgs& a, int bx, int by, int bz,
+                                        unsigned char* smem, int* s_abort) {
     using S = typename Tr::S;
     using C = typename Tr::C;
     constexpr int NS = kRing;
-    using L = TBLayout<V, NW, R, T, NS, S>;
+    constexpr int NSR = rho_slots<MODE, NS, T>();
+    using L = TBLayout<V, NW, R, T, NS, S, NSR>;
     constexpr int EX = L::EX, EY = L::EY, PLANE = L::PLANE, LPLANE = L::LPLANE;
     constexpr uint32_t kPlaneBytes = PLANE * sizeof(S);
+    // bytes landing per ring slot: the grid plane, and the rho plane of the same k
+    constexpr uint32_t kSlotBytes = (NSR > 0 ? 2 : 1) * kPlaneBytes;
     constexpr int OY = EY - 2 * T;
     static_assert(OY >= 1, "tile too small for the depth");
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     S* ring = reinterpret_cast<S*>(smem + L::HEADER);
     S* lvl = ring + NS * PLANE;
+    S* rring = reinterpret_cast<S*>(smem + L::RHO_OFF);
 
     const unsigned FULL = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -152,19 +167,19 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a
     }
     __syncthreads();
     int issued = 0;  // planes issued so far (thread 0 only)
+    int rslot = 0;   // rho slot of plane Zlo + issued (thread 0 only)
     if (tid == 0) {
 #pragma unroll 1
         for (int i = 0; i < NS && i < M; ++i) {
-            mbar_arrive_expect_tx(&bars[i], kPlaneBytes);
+            mbar_arrive_expect_tx(&bars[i], kSlotBytes);
             tma_load_3d(ring + i * PLANE, tmap, &bars[i], X0, Y0, Zlo + i);
+            if (NSR > 0) tma_load_3d(rring + i * PLANE, tmap_rho, &bars[i], X0, Y0, Zlo + i);
         }
         issued = min(NS, M);
+        rslot = issued;  // NS < NSR
     }
 
     C rr[T][3][R][V];  // per level s < T: 3 planes (roles rotate with the step) of level s
-    // rho FIFO (MODE_RHS): rq[j] = rho at plane Zlo+m-j
-    constexpr int kRQ = (MODE == MODE_RHS) ? T + 1 : 1;
-    C rq[kRQ][R][V];
 #pragma unroll
     for (int s = 0; s < T; ++s)
 #pragma unroll
@@ -173,15 +188,8 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a
             for (int r = 0; r < R; ++r)
 #pragma unroll
                 for (int e = 0; e < V; ++e) rr[s][j][r][e] = C(0);
-#pragma unroll
-    for (int j = 0; j < kRQ; ++j)
-#pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int e = 0; e < V; ++e) rq[j][r][e] = C(0);
 
     const C c6 = Tr::sixth();
-    const S* rho = static_cast<const S*>(a.rho);
     S* dst = static_cast<S*>(a.dst);
     S* grad = static_cast<S*>(a.grad);
     const long long rowoff0 = (long long)gy0 * g.px + gx0;  // valid only when used
@@ -191,20 +199,6 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a
     const int lrow_bot = (R == 1) ? w : 2 * w + 1;
     const int lrow_above = lrow_top - 1, lrow_below = lrow_bot + 1;
     const int prow_above = row0 - 1, prow_below = row0 + R;
-
-    auto load_rho = [&](int pr, int r, C (&dstv)[V]) {
-        const bool zinr = (pr >= 1) && (pr <= g.nz);
-        const long long o = g.plane * pr + rowoff0 + (long long)r * g.px;
-        if (zinr && all_in[r]) {
-            const Vec<S, V> q = ldg_vec<S, V>(rho + o);
-#pragma unroll
-            for (int e = 0; e < V; ++e) dstv[e] = Tr::ld(q.v[e]);
-        } else {
-#pragma unroll
-            for (int e = 0; e < V; ++e)
-                dstv[e] = (zinr && inxy[r][e]) ? Tr::ld(rho[o + e]) : C(0);
-        }
-    };
 
     // boundary-gradient accumulation (MODE_ADJ): face flags per cell, 5 bits each
     // (x = 1, x = nx, y = 1, y = ny, owned), precomputed; z faces are uniform per plane
@@ -253,6 +247,7 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a
     };
 
     int cur_m = 0;  // step being executed (for the clean-up after a timeout)
+    int rs = 0;     // rho slot of plane Zlo + m (MODE_RHS)
     // One step of the k-march; PH = m mod 6 fixes slot, parity and rotation.
     auto step = [&](auto ph, int m) -> bool {
         constexpr int PH = decltype(ph)::value;
@@ -275,16 +270,6 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a
 #pragma unroll
                 for (int e = 0; e < V; ++e) rr[0][NEW][r][e] = Tr::ld(t.v[e]);
             }
-            if (MODE == MODE_RHS) {
-#pragma unroll
-                for (int j = kRQ - 1; j >= 1; --j)
-#pragma unroll
-                    for (int r = 0; r < R; ++r)
-#pragma unroll
-                        for (int e = 0; e < V; ++e) rq[j][r][e] = rq[j - 1][r][e];
-#pragma unroll
-                for (int r = 0; r < R; ++r) load_rho(p0, r, rq[0][r]);
-            }
             if (MODE == MODE_ADJ) adj_acc(rr[0][NEW], p0);
         }
         // ---- levels 1..T
@@ -306,6 +291,15 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a
                 vn = *reinterpret_cast<const Vec<S, V>*>(nb + lrow_above * EX + mycol);
                 vs = *reinterpret_cast<const Vec<S, V>*>(nb + lrow_below * EX + mycol);
             }
+            // rho at plane q (MODE_RHS): rho slot of relative plane m - s
+            Vec<S, V> vr[R];
+            if (MODE == MODE_RHS) {
+                const int sl = (rs >= s) ? rs - s : rs - s + (NSR > 0 ? NSR : 1);
+#pragma unroll
+                for (int r = 0; r < R; ++r)
+                    vr[r] = *reinterpret_cast<const Vec<S, V>*>(rring + sl * PLANE +
+                                                                (row0 + r) * EX + mycol);
+            }
             C out[R][V];
 #pragma unroll
             for (int r = 0; r < R; ++r) {
@@ -324,8 +318,7 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a
                         sum = Tr::add(sum, ss);
                         sum = Tr::add(sum, rr[s - 1][OLD][r][e]);
                         sum = Tr::add(sum, rr[s - 1][NEW][r][e]);
-                        if (MODE == MODE_RHS)
-                            sum = Tr::add(sum, rq[(MODE == MODE_RHS) ? s : 0][r][e]);
+                        if (MODE == MODE_RHS) sum = Tr::add(sum, Tr::ld(vr[r].v[e]));
                         const C val = Tr::rnd(Tr::mul(sum, c6));
                         out[r][e] = (FAST || inxy[r][e]) ? val : rr[s - 1][CUR][r][e];
                     }
@@ -370,12 +363,20 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const TBArgs& a
         __syncthreads();
         if (*s_abort) return false;
         // the slot of plane Zlo+m-1 is free now: refill it with plane Zlo+m-1+NS
+        // (and the rho plane of that k into the rho slot whose last reader, level
+        // T at step m-NS+... , has finished: see rho_slots)
         if (tid == 0 && m >= 1 && issued < M) {
             fence_proxy_async_smem();
-            mbar_arrive_expect_tx(&bars[PSLOT], kPlaneBytes);
+            mbar_arrive_expect_tx(&bars[PSLOT], kSlotBytes);
             tma_load_3d(ring + PSLOT * PLANE, tmap, &bars[PSLOT], X0, Y0, Zlo + issued);
+            if (NSR > 0) {
+                tma_load_3d(rring + rslot * PLANE, tmap_rho, &bars[PSLOT], X0, Y0,
+                            Zlo + issued);
+                rslot = (rslot + 1 == NSR) ? 0 : rslot + 1;
+            }
             ++issued;
         }
+        if (MODE == MODE_RHS) rs = (rs + 1 == NSR) ? 0 : rs + 1;
         return true;
     };
 
@@ -424,19 +425,21 @@ __device__ __forceinline__ bool tile_inside_xy(const TBArgs& a, int bx, int by) 
 
 template <class Tr, int V, int NW, int R, int T, int MODE, int NS, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB)
-    tb_sweep_kernel(const __grid_constant__ CUtensorMap tmap, const TBArgs a) {
+    tb_sweep_kernel(const __grid_constant__ CUtensorMap tmap,
+                    const __grid_constant__ CUtensorMap tmap_rho, const TBArgs a) {
     static_assert(NS == kRing, "the k-march is unrolled by the ring size");
     extern __shared__ __align__(1024) unsigned char smem[];
     __shared__ int s_abort;
     if (threadIdx.x == 0) {
         s_abort = 0;
         prefetch_tmap(&tmap);
+        if (MODE == MODE_RHS) prefetch_tmap(&tmap_rho);
     }
     const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
     if (tile_inside_xy<V, NW, R, T>(a, bx, by))
-        tb_tile<Tr, V, NW, R, T, MODE, true>(&tmap, a, bx, by, bz, smem, &s_abort);
+        tb_tile<Tr, V, NW, R, T, MODE, true>(&tmap, &tmap_rho, a, bx, by, bz, smem, &s_abort);
     else
-        tb_tile<Tr, V, NW, R, T, MODE, false>(&tmap, a, bx, by, bz, smem, &s_abort);
+        tb_tile<Tr, V, NW, R, T, MODE, false>(&tmap, &tmap_rho, a, bx, by, bz, smem, &s_abort);
 }
 
 }  // namespace jac

@@ -3,13 +3,15 @@
 
 namespace jac {
 
-// depths 1..4: deeper passes need more registers than 1024-thread CTAs have
-// (they spill) and run slower than depth 4
+// the right-hand side is staged in shared memory by TMA (NS + T slots), which
+// bounds the depth at 6 (227 KB of shared memory per CTA for FP32)
 static const TBEntry kTB[] = {
     JAC_TB(BF16, 2, 32, 1, MODE_RHS, 6),
     JAC_TB(BF16, 2, 32, 2, MODE_RHS, 6),
     JAC_TB(BF16, 2, 32, 3, MODE_RHS, 6),
     JAC_TB(BF16, 2, 32, 4, MODE_RHS, 6),
+    JAC_TB(BF16, 2, 32, 5, MODE_RHS, 6),
+    JAC_TB(BF16, 2, 32, 6, MODE_RHS, 6),
 };
 JAC_TABLE(tb_entries_bf16_rhs, kTB)
 

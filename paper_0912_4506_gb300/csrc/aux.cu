@@ -102,6 +102,30 @@ __global__ void emulated_add_kernel(const double* __restrict__ a, const double* 
     }
 }
 
+// Exact widening of a float to double on the integer pipes (IEEE 754 binary32
+// -> binary64: same sign, exponent rebiased by 1023 - 127, fraction shifted left
+// by 29), for normal numbers and zeros; subnormals, infinities and NaNs take the
+// conversion instruction.  Keeps the FP64 pipe, which bounds the residual step,
+// for the arithmetic.
+static __device__ __noinline__ double f32_to_f64_unit(float f) { return (double)f; }
+
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const uint32_t b = __float_as_uint(f);
+    const uint32_t ex = (b >> 23) & 0xFFu;
+    const bool zero = (b & 0x7FFFFFFFu) == 0u;
+    const uint32_t hi = (b & 0x80000000u) |
+                        (zero ? 0u : (((ex + 896u) << 20) | ((b & 0x7FFFFFu) >> 3)));
+    const uint32_t lo = zero ? 0u : (b << 29);
+    double r = __hiloint2double((int)hi, (int)lo);
+    const bool special = !zero && (ex == 0u || ex == 0xFFu);
+    if (__any_sync(__activemask(), special)) {
+        if (special) r = f32_to_f64_unit(f);
+    }
+    return r;
+}
+__device__ __forceinline__ double widen(float f) { return f32_to_f64(f); }
+__device__ __forceinline__ double widen(double d) { return d; }
+
 // Residual step of the refinement, fused and streaming in k.  For every interior
 // cell, with u'(c) = u_in(c) + (double) e(c) on interior cells and u_in(c) on the
 // boundary layer:
@@ -109,13 +133,17 @@ __global__ void emulated_add_kernel(const double* __restrict__ a, const double* 
 //     rho   = ((((( u'[i-1] + u'[i+1]) + u'[j-1]) + u'[j+1]) + u'[k-1]) + u'[k+1]) - 6.0*u'
 // in FP64 (product rounded before the subtraction), rho rounded to the low
 // precision.  The kernel is bound by the FP64 pipe (2 ops/clk/SM on GB300), so
-// u' is formed once per cell: a CTA of RES_ROWS + 2 warps covers 32 x-cells of
-// RES_ROWS rows plus one halo row above and below; each warp forms u' for its
-// row of the plane streaming in, keeps the k-1, k, k+1 values in registers, and
-// shares the k plane through shared memory (y-neighbours) and shuffles (x); the
-// halo warps only form u'.  Same bits as "accumulate everywhere, then take the
-// residual" (u' of a cell is the same FP64 sum wherever it is formed).
-constexpr int RES_ROWS = 8;
+// every FP64 instruction a warp issues should produce cells: a CTA of
+// RES_ROWS + 2 warps covers RES_ROWS rows plus one halo row above and below, and
+// each warp's 32 lanes cover 32 consecutive columns of which the 30 inner ones
+// are outputs (the two edge lanes supply the x-neighbours), so no lane forms a
+// second u'.  Each warp forms u' for its row of the plane streaming in, keeps the
+// k-1, k, k+1 values in registers, and shares the k plane through shared memory
+// (y-neighbours) and shuffles (x); the halo warps only form u'.  Same bits as
+// "accumulate everywhere, then take the residual" (u' of a cell is the same FP64
+// sum wherever it is formed).
+constexpr int RES_ROWS = 16;
+constexpr int RES_OUT_X = 30;
 
 template <class Lo>
 __global__ void __launch_bounds__((RES_ROWS + 2) * 32)
@@ -125,36 +153,35 @@ __global__ void __launch_bounds__((RES_ROWS + 2) * 32)
     __shared__ double s_u[2][RES_ROWS + 2][32];
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;  // w = 0 and RES_ROWS+1: halo
-    const int x = 1 + (int)blockIdx.x * 32 + lane;
+    const int x = (int)blockIdx.x * RES_OUT_X + lane;          // lanes 0 and 31: halo
     const int y = (int)blockIdx.y * RES_ROWS + w;  // row of this warp (0 .. ny+1 possible)
     const int k0 = 1 + (int)blockIdx.z * kchunk;
     const int k1 = min(gu.nz, k0 + kchunk - 1);
     const int xc = min(x, gu.nx + 1);  // clamped column (loads stay inside the array)
     const int yc = min(y, gu.ny + 1);
-    const bool row_in = y >= 1 && y <= gu.ny;
-    const bool cell_in = row_in && x <= gu.nx;      // interior in x and y
-    const bool compute = w >= 1 && w <= RES_ROWS && cell_in;
+    const bool cell_in = y >= 1 && y <= gu.ny && x >= 1 && x <= gu.nx;  // interior in x, y
+    const bool compute = w >= 1 && w <= RES_ROWS && lane >= 1 && lane <= RES_OUT_X && cell_in;
     const int ktop = gu.nz + 1;
+    const long long ou = gu.lin(xc, yc, 0), ol = gl.lin(xc, yc, 0);
 
-    // u' of this lane's column at plane kk (boundary planes and cells: u_in)
-    auto uprime = [&](int xx, int kk) -> double {
-        const double u = __ldg(u_in + gu.lin(xx, yc, kk));
-        const bool in = row_in && xx >= 1 && xx <= gu.nx && kk >= 1 && kk <= gu.nz;
-        return in ? __dadd_rn(u, (double)Lo::ld(__ldg(e + gl.lin(xx, yc, kk)))) : u;
+    // u' of this lane's cell at plane kk (boundary planes and cells: u_in)
+    auto uprime = [&](int kk) -> double {
+        const double u = __ldg(u_in + ou + gu.plane * kk);
+        const double d = widen(Lo::ld(__ldg(e + ol + gl.plane * kk)));
+        const bool in = cell_in && kk >= 1 && kk <= gu.nz;
+        return in ? __dadd_rn(u, d) : u;
     };
-    double dn = uprime(xc, k0 - 1);
-    double ct = uprime(xc, k0);
-    double up = uprime(xc, min(k0 + 1, ktop));
+    double dn = uprime(k0 - 1);
+    double ct = uprime(k0);
+    double up = uprime(min(k0 + 1, ktop));
     int buf = 0;
     s_u[buf][w][lane] = ct;
     __syncthreads();
     for (int k = k0; k <= k1; ++k) {
         // next plane first (its loads overlap this step's arithmetic)
-        const double up2 = uprime(xc, min(k + 2, ktop));
-        double left = __shfl_up_sync(FULL, ct, 1);
-        double right = __shfl_down_sync(FULL, ct, 1);
-        if (lane == 0) left = uprime(x - 1, k);
-        if (lane == 31 || x == gu.nx) right = uprime(min(x + 1, gu.nx + 1), k);
+        const double up2 = uprime(min(k + 2, ktop));
+        const double left = __shfl_up_sync(FULL, ct, 1);
+        const double right = __shfl_down_sync(FULL, ct, 1);
         if (compute) {
             double s = __dadd_rn(left, right);
             s = __dadd_rn(s, s_u[buf][w - 1][lane]);
@@ -162,8 +189,8 @@ __global__ void __launch_bounds__((RES_ROWS + 2) * 32)
             s = __dadd_rn(s, dn);
             s = __dadd_rn(s, up);
             const double r = __dsub_rn(s, __dmul_rn(6.0, ct));
-            u_out[gu.lin(x, y, k)] = ct;
-            rho[gl.lin(x, y, k)] = Lo::st((typename Lo::C)r);
+            u_out[ou + gu.plane * k] = ct;
+            rho[ol + gl.plane * k] = Lo::st((typename Lo::C)r);
         }
         dn = ct;
         ct = up;
@@ -178,11 +205,12 @@ cudaError_t launch_residual(const double* u_in, double* u_out, const Geom& gu, c
                             void* rho, int lo_dtype, const Geom& glo, cudaStream_t st) {
     const dim3 block((RES_ROWS + 2) * 32);
     // k-chunks of at least 16 planes, enough CTAs for several waves
-    const long long tiles = (long long)((gu.nx + 31) / 32) * ((gu.ny + RES_ROWS - 1) / RES_ROWS);
+    const int tx = (gu.nx + RES_OUT_X - 1) / RES_OUT_X, ty = (gu.ny + RES_ROWS - 1) / RES_ROWS;
+    const long long tiles = (long long)tx * ty;
     int chunks = (int)std::max<long long>(1, std::min<long long>(gu.nz / 16, 8192 / tiles + 1));
     const int kchunk = (gu.nz + chunks - 1) / chunks;
     chunks = (gu.nz + kchunk - 1) / kchunk;
-    const dim3 grid((gu.nx + 31) / 32, (gu.ny + RES_ROWS - 1) / RES_ROWS, chunks);
+    const dim3 grid(tx, ty, chunks);
     if (lo_dtype == 1) {
         residual_kernel<F32><<<grid, block, 0, st>>>(u_in, u_out, gu,
                                                      static_cast<const float*>(e),

@@ -38,12 +38,31 @@ def test_rhs_sweeps_bit_exact(dtype, shape):
             assert np.array_equal(got, want), (n, t)
 
 
+def _special_interior(nx, ny, nz, dtype, seed):
+    """Corrections mixing zeros of both signs, subnormal and huge values with
+    ordinary ones (the widening of e to FP64 has separate paths for them)."""
+    rng = np.random.default_rng(seed)
+    px = inputs.row_pitch(nx, dtype)
+    vals = np.array([0.0, -0.0, 1e-40, -3e-42, 2.0 ** -149, 1e30, -1e30, 0.5, -0.25,
+                     1.2e-38, 3.0e38], dtype=np.float64)
+    a = np.zeros((nz + 2, ny + 2, px), dtype=np.float64)
+    pick = rng.integers(0, 3 * len(vals), (nz, ny, nx))
+    reg = (rng.random((nz, ny, nx)) - 0.5) * 1e-3
+    a[1:-1, 1:-1, 1:nx + 1] = np.where(pick < len(vals), vals[np.minimum(pick, len(vals) - 1)],
+                                       reg)
+    return inputs.to_dtype(a, dtype, px=px)
+
+
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-def test_residual_accumulate_bit_exact(dtype):
+@pytest.mark.parametrize("case", ["random", "special", "ragged"])
+def test_residual_accumulate_bit_exact(dtype, case):
     from paper_0912_4506_gb300 import api
-    nx, ny, nz = 53, 41, 19
+    nx, ny, nz = (97, 50, 33) if case == "ragged" else (53, 41, 19)
     u = inputs.uniform_grid_f64(nx, ny, nz, px=inputs.row_pitch(nx, "f64")) * 100.0 - 50.0
-    e = _rand_interior(nx, ny, nz, dtype, 3, scale=1e-3)
+    if case == "special":
+        e = _special_interior(nx, ny, nz, dtype, 4)
+    else:
+        e = _rand_interior(nx, ny, nz, dtype, 3, scale=1e-3)
     e_same = np.zeros(u.shape, dtype=e.dtype)  # the oracle takes one row pitch for both
     w = min(u.shape[2], e.shape[2])
     e_same[:, :, :w] = e[:, :, :w]

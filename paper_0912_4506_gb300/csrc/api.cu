@@ -7,7 +7,6 @@
 #include <algorithm>
 #include <cstdint>
 #include <cstdlib>
-#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -79,40 +78,12 @@ int make_map(CUtensorMap* map, const jacobi_s* h, void* base, int bx, int by) {
     return r == CUDA_SUCCESS ? JAC_OK : JAC_ECUDA;
 }
 
-// Which compiled shape (warps NW, rows per thread R, CTAs per SM MINB) serves a
-// depth.  By default the two-rows-per-thread kernels, which are compiled only at
-// the depths where they measured faster; JACOBI_TB_SHAPE="NW,R[,MINB]" selects
-// another compiled shape for every depth that has one.
-struct ShapePref {
-    bool env = false;
-    int nw = 0, r = 0, minb = 1;
-    bool operator()(const TBEntry& e) const {
-        if (!env) return e.R == 2;
-        return e.NW == nw && e.R == r && e.minb == minb;
-    }
-};
-
-ShapePref shape_pref() {
-    ShapePref p;
-    if (const char* e = getenv("JACOBI_TB_SHAPE")) {
-        int a = 0, b = 0, c = 1;
-        if (sscanf(e, "%d,%d,%d", &a, &b, &c) >= 2 && a > 0 && b > 0 && c > 0) {
-            p.env = true;
-            p.nw = a;
-            p.r = b;
-            p.minb = c;
-        }
-    }
-    return p;
-}
-
 const std::vector<TBEntry>& tb_table(int dtype, int mode) {
     static std::vector<TBEntry> tabs[3][3];
     static std::once_flag once;
     std::call_once(once, [] {
-        std::vector<TBEntry> all[3][3];
-        auto add = [&all](const TBEntry* p, int n) {
-            for (int i = 0; i < n; ++i) all[p[i].dtype][p[i].mode].push_back(p[i]);
+        auto add = [](const TBEntry* p, int n) {
+            for (int i = 0; i < n; ++i) tabs[p[i].dtype][p[i].mode].push_back(p[i]);
         };
         int n;
         const TBEntry* p;
@@ -120,26 +91,12 @@ const std::vector<TBEntry>& tb_table(int dtype, int mode) {
         p = tb_entries_f32(&n); add(p, n);
         p = tb_entries_f32_rhs(&n); add(p, n);
         p = tb_entries_f32_adj(&n); add(p, n);
-        p = tb_entries_f32_rows(&n); add(p, n);
         p = tb_entries_bf16(&n); add(p, n);
         p = tb_entries_bf16_rhs(&n); add(p, n);
-        p = tb_entries_bf16_rows(&n); add(p, n);
-        // one entry per depth: the preferred shape where compiled, else the first
-        const ShapePref pref = shape_pref();
-        for (int d = 0; d < 3; ++d)
-            for (int m = 0; m < 3; ++m) {
-                for (const TBEntry& e : all[d][m]) {
-                    TBEntry* have = nullptr;
-                    for (TBEntry& x : tabs[d][m])
-                        if (x.T == e.T) have = &x;
-                    if (!have)
-                        tabs[d][m].push_back(e);
-                    else if (pref(e) && !pref(*have))
-                        *have = e;
-                }
-                std::sort(tabs[d][m].begin(), tabs[d][m].end(),
+        for (auto& d : tabs)
+            for (auto& v : d)
+                std::sort(v.begin(), v.end(),
                           [](const TBEntry& x, const TBEntry& y) { return x.T < y.T; });
-            }
     });
     return tabs[dtype][mode];
 }
@@ -217,7 +174,7 @@ int pick_chunks(int nz, int T, long long tiles, int slots) {
 TBGeom tb_geom(const jacobi_s* h, const TBEntry& e) {
     TBGeom r{};
     const int A = 16 / elem_size(h->dtype);
-    const int EX = 32 * e.V, EY = e.NW * e.R, T = e.T;
+    const int EX = 32 * e.V, EY = e.NW, T = e.T;
     r.ox = ((EX - 2 * T) / A) * A;
     r.oy = EY - 2 * T;
     r.ok = r.ox >= A && r.oy >= 1;
@@ -291,13 +248,12 @@ int check_grid_args(int nx, int ny, int nz, int dtype, long long pitch) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Depth used when the caller leaves it to the planner (t = 0): the fastest
-// measured at 512^3 on GB300 for each kind of sweep.  FP64 is bound by the FP64
-// pipe, so blocking cannot help it; plain FP32/bf16 sweeps peak at depth 2 (two
-// rows per thread, two CTAs per SM), correction sweeps at 4, adjoint sweeps at 3.
+// Depth used when the caller leaves it to the planner (t = 0): FP64 is bound by
+// the FP64 pipe, so blocking cannot help it (plain streaming kernel); FP32 and
+// bf16 sweeps of every kind run fastest at depth 4 on GB300 at 512^3.
 int default_t(int dtype, int mode) {
-    if (dtype == JAC_F64) return 1;
-    return mode == MODE_PLAIN ? 2 : mode == MODE_RHS ? 4 : 3;
+    (void)mode;
+    return dtype == JAC_F64 ? 1 : 4;
 }
 
 // Run nsweeps of `mode` as a sequence of passes.  kernel: JAC_KERNEL_*.
@@ -368,7 +324,7 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
             info_only->tile_x = gm.ox;
             info_only->tile_y = gm.oy;
             info_only->ext_x = 32 * e->V;
-            info_only->ext_y = e->NW * e->R;
+            info_only->ext_y = e->NW;
             info_only->kchunk = gm.kz;
             info_only->threads = e->NW * 32;
             info_only->smem_bytes = (int)e->smem;
@@ -384,7 +340,7 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         const TBEntry* e = find_entry(tab, depths[p]);
         const TBGeom gm = tb_geom(h, *e);
         if (!gm.ok) return JAC_EUNSUPPORTED;
-        const int EX = 32 * e->V, EY = e->NW * e->R;
+        const int EX = 32 * e->V, EY = e->NW;
         if (EX != h->map_box_x || EY != h->map_box_y) {
             if (make_map(&h->map_a, h, h->a, EX, EY) != JAC_OK) return JAC_ECUDA;
             if (make_map(&h->map_b, h, h->b, EX, EY) != JAC_OK) return JAC_ECUDA;
@@ -394,7 +350,6 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         TBArgs args;
         args.g = h->g;
         args.dst = cur_b ? h->a : h->b;
-        args.rho = rho;
         args.grad = grad;
         args.ox = gm.ox;
         args.x0_first = gm.x0_first;

@@ -216,9 +216,8 @@ int jacobi_batch_create(jacobi_batch_t* out, int count, const int* dims,
     b->nitems = (int)items.size();
 
     const void* kern = batch_kernel_ptr(dtype);
-    b->smem = (dtype == JAC_F32)
-                  ? TBLayout<kBatchV, kBatchNW, 1, kBatchTMax, kRing, float>::bytes()
-                  : TBLayout<kBatchV, kBatchNW, 1, kBatchTMax, kRing, uint16_t>::bytes();
+    b->smem = (dtype == JAC_F32) ? TBLayout<kBatchV, kBatchNW, kBatchTMax, kRing, float>::bytes()
+                                 : TBLayout<kBatchV, kBatchNW, kBatchTMax, kRing, uint16_t>::bytes();
     int occ = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) !=
             cudaSuccess ||

@@ -48,12 +48,12 @@ __device__ __forceinline__ void fence_proxy_async_global() {
 template <class Tr, int T>
 __device__ __forceinline__ void batch_tile(const CUtensorMap* map, const TBArgs& a, int bx,
                                            int by, int bz, unsigned char* smem, int* s_abort) {
-    if (tile_inside_xy<kBatchV, kBatchNW, 1, T>(a, bx, by))
-        tb_tile<Tr, kBatchV, kBatchNW, 1, T, MODE_PLAIN, true>(map, nullptr, a, bx, by, bz, smem,
-                                                               s_abort);
+    if (tile_inside_xy<kBatchV, kBatchNW, T>(a, bx, by))
+        tb_tile<Tr, kBatchV, kBatchNW, T, MODE_PLAIN, true>(map, nullptr, a, bx, by, bz, smem,
+                                                            s_abort);
     else
-        tb_tile<Tr, kBatchV, kBatchNW, 1, T, MODE_PLAIN, false>(map, nullptr, a, bx, by, bz, smem,
-                                                                s_abort);
+        tb_tile<Tr, kBatchV, kBatchNW, T, MODE_PLAIN, false>(map, nullptr, a, bx, by, bz, smem,
+                                                             s_abort);
 }
 
 template <class Tr>
@@ -92,7 +92,6 @@ __global__ void __launch_bounds__(kBatchNW * 32, 1) tb_batch_kernel(const BatchA
         TBArgs a;
         a.g = G.g;
         a.dst = (item.pass & 1) ? G.a : G.b;
-        a.rho = nullptr;
         a.grad = nullptr;
         a.ox = pg.ox;
         a.x0_first = pg.x0_first;

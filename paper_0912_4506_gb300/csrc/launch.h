@@ -22,11 +22,9 @@ struct TBEntry {
     int dtype;      // 0 f64, 1 f32, 2 bf16
     int mode;       // MODE_PLAIN, MODE_RHS, MODE_ADJ
     int V;          // x cells per lane (extended tile width 32*V)
-    int NW;         // warps per CTA
-    int R;          // rows per thread (extended tile height NW*R)
+    int NW;         // warps = rows of the extended tile
     int T;          // temporal-blocking depth
     int NS;         // TMA ring slots
-    int minb;       // CTAs per SM the register allocation allows
     size_t smem;    // dynamic shared memory bytes
     TBLaunchFn launch;
     const void* kernel;
@@ -47,11 +45,9 @@ struct PlainEntry {
 // Tables provided by the per-dtype translation units.
 const TBEntry* tb_entries_f64(int* n);
 const TBEntry* tb_entries_f32(int* n);
-const TBEntry* tb_entries_f32_rows(int* n);
 const TBEntry* tb_entries_f32_rhs(int* n);
 const TBEntry* tb_entries_f32_adj(int* n);
 const TBEntry* tb_entries_bf16(int* n);
-const TBEntry* tb_entries_bf16_rows(int* n);
 const TBEntry* tb_entries_bf16_rhs(int* n);
 const PlainEntry* plain_entry_f64();
 const PlainEntry* plain_entries_f64(int* n);  // all emulation variants

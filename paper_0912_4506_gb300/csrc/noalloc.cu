@@ -84,7 +84,7 @@ struct Pass {
 
 bool pass_geometry(const TBEntry* e, const Geom& g, int dtype, int sms, Pass* p) {
     const int A = 16 / esize(dtype);
-    const int EX = 32 * e->V, EY = e->NW * e->R, T = e->T;
+    const int EX = 32 * e->V, EY = e->NW, T = e->T;
     p->e = e;
     p->ox = ((EX - 2 * T) / A) * A;
     p->oy = EY - 2 * T;
@@ -131,7 +131,7 @@ int depth_at_most(int dtype, const Geom& g, int want) {
         const TBEntry* e = entry_for(dtype, d);
         if (!e) continue;
         const int A = 16 / esize(dtype);
-        if (((32 * e->V - 2 * d) / A) * A >= A && e->NW * e->R - 2 * d >= 1) return d;
+        if (((32 * e->V - 2 * d) / A) * A >= A && e->NW - 2 * d >= 1) return d;
     }
     return 0;
 }
@@ -194,7 +194,7 @@ extern "C" int jacobi_sweep_noalloc(int nx, int ny, int nz, int dtype, void* gri
             Pass p;
             if (d == 0 || !pass_geometry(entry_for(dtype, d), g, dtype, sms, &p))
                 return JAC_EUNSUPPORTED;
-            const int EX = 32 * p.e->V, EY = p.e->NW * p.e->R;
+            const int EX = 32 * p.e->V, EY = p.e->NW;
             if (EX != box_x || EY != box_y) {
                 if (!encode(&map_grid, dtype, g, grid, EX, EY) ||
                     !encode(&map_other, dtype, g, other, EX, EY))
@@ -205,7 +205,6 @@ extern "C" int jacobi_sweep_noalloc(int nx, int ny, int nz, int dtype, void* gri
             TBArgs a;
             a.g = g;
             a.dst = cur_other ? grid : other;
-            a.rho = nullptr;
             a.grad = nullptr;
             a.ox = p.ox;
             a.x0_first = p.x0_first;

@@ -9,19 +9,17 @@
 // inside the CTA:
 //
 //  * the CTA owns an output tile (OX x OY cells, a chunk of k-planes) and loads
-//    the extended tile (EX x EY = (32*V) x (NW*R) cells, a T-cell halo around the
+//    the extended tile (EX x EY = (32*V) x NW cells, a T-cell halo around the
 //    output tile) plane by plane with TMA into a ring of NS shared-memory slots;
 //  * it marches k.  At step m, level 0 is plane Zlo+m (just loaded), and level s
 //    (1..T) computes plane Zlo+m-s from level s-1's planes Zlo+m-s-1..Zlo+m-s+1:
 //    the k-neighbours come from the thread's own registers (a 3-plane rotation
-//    per level), the x-neighbours by warp shuffles, the y-neighbours from the
-//    thread's own rows or, at its strip's edges, from a double-buffered shared-
-//    memory copy of every strip's edge rows written in the previous step;
+//    per level), the x-neighbours by warp shuffles, the y-neighbours from a
+//    double-buffered shared-memory plane per level written in the previous step;
 //  * one __syncthreads per step; level T's planes inside the chunk are written
 //    to global memory for the cells of the output tile.
 //
-// Every thread owns V consecutive x cells of R rows (lane -> x, warp -> a strip
-// of R rows).
+// Every thread owns V consecutive x cells of one row (lane -> x, warp -> y).
 // Level s is valid on rows [s, EY-s) and columns [s, EX-s) of the extended tile;
 // warps outside that row range skip the level.  Cells off the interior (the
 // boundary layer, the row padding and anything outside the array, which TMA
@@ -36,9 +34,9 @@
 // per-cell boundary selects.
 //
 // Modes: MODE_PLAIN (Eq. 1), MODE_RHS (the refinement's correction sweep, adds
-// rho before the product), MODE_ADJ (the adjoint sweep on a zero boundary, and
-// accumulation of RN(1/6)*lambda at the face-neighbouring interior cells into
-// the boundary gradient).
+// rho before the product; rho's planes arrive by TMA beside the grid's), MODE_ADJ
+// (the adjoint sweep on a zero boundary, and accumulation of RN(1/6)*lambda at
+// the face-neighbouring interior cells into the boundary gradient).
 #pragma once
 
 #include <type_traits>
@@ -54,7 +52,6 @@ constexpr int kRing = 6;  // TMA ring slots (the unroll period)
 struct TBArgs {
     Geom g;
     void* dst;          // output grid of the pass (level T)
-    const void* rho;    // MODE_RHS: right-hand side grid (same layout)
     void* grad;         // MODE_ADJ: boundary gradient grid (same layout)
     int ox;             // output tile width (multiple of the TMA alignment)
     int x0_first;       // x origin of tile 0's extended tile (aligned, may be < 0)
@@ -62,31 +59,29 @@ struct TBArgs {
     int* status;        // device status word (timeouts)
 };
 
-template <int V, int NW, int R, int T, int NS, class S, int NSR = 0>
+// Shared memory of one CTA: mbarriers (HEADER), the TMA ring (NS planes), the
+// level buffers (two per level 1..T-1), one guard row, and for correction sweeps
+// the rho ring (NSR planes).  The rows just above and below the extended tile are
+// read without clamping (their values only reach cells outside the valid region
+// of the level being computed); the header's tail and the guard row keep those
+// reads inside the allocation.
+template <int V, int NW, int T, int NS, class S, int NSR = 0>
 struct TBLayout {
     static constexpr int EX = 32 * V;
-    static constexpr int EY = NW * R;                 // rows of the extended tile
-    static constexpr int PLANE = EX * EY;             // one TMA ring slot
-    static constexpr int LROWS = (R == 1) ? EY : 2 * NW;  // rows kept per level plane
-    static constexpr int LPLANE = EX * LROWS;
+    static constexpr int EY = NW;
+    static constexpr int PLANE = EX * EY;
     static constexpr int NLB = (T > 1) ? 2 * (T - 1) : 0;  // level buffers
-    // mbarriers at the start; the header's last row-sized stretch and one row
-    // after the level buffers are guard rows, so that the rows just above and
-    // below the extended tile can be read without clamping (their values only
-    // reach cells outside the valid region of the level being computed).  The
-    // NSR slots of the right-hand-side ring (correction sweeps) follow.
-    static constexpr int HEADER = 1024;
+    static constexpr int HEADER = 1024;                      // mbarriers, aligned
     static_assert(EX * sizeof(S) + 64 <= HEADER, "guard row overlaps the mbarriers");
     static constexpr size_t RHO_OFF =
-        HEADER + (size_t)NS * PLANE * sizeof(S) + (size_t)NLB * LPLANE * sizeof(S) +
-        (size_t)EX * sizeof(S);
+        HEADER + (size_t)(NS + NLB) * PLANE * sizeof(S) + (size_t)EX * sizeof(S);
     static_assert(RHO_OFF % 128 == 0, "TMA destinations must stay 128-byte aligned");
     static constexpr size_t bytes() { return RHO_OFF + (size_t)NSR * PLANE * sizeof(S); }
 };
 
-// Slots of the right-hand-side ring for depth T: a plane is issued together with
-// the grid plane of the same k, NS-1 steps before its first use, and is read by
-// the levels 1..T, so NS + T slots keep every plane until its last reader is done.
+// Slots of the rho ring for depth T (correction sweeps): rho plane P is issued
+// with grid plane P, NS - 1 steps before level 1 reads it, and level T reads it
+// T - 1 steps after that, so NS + T slots keep it until its last reader is done.
 template <int MODE, int NS, int T>
 constexpr int rho_slots() {
     return MODE == MODE_RHS ? NS + T : 0;
@@ -98,13 +93,7 @@ using IC = std::integral_constant<int, N>;
 // One output tile of one temporally-blocked pass.  `smem` is the CTA's dynamic
 // shared memory (TBLayout), `s_abort` a shared flag.  Returns false when a TMA
 // wait timed out (status already recorded).  All threads of the CTA call it.
-//
-// Thread (lane, w) owns V consecutive x cells of the R rows w*R .. w*R+R-1 of the
-// extended tile.  In-strip y-neighbours come from the thread's own registers;
-// only the strip's first and last rows go through shared memory (R == 1: the one
-// row), so a level costs two shared-memory row reads and at most two row writes
-// per R*V cells.
-template <class Tr, int V, int NW, int R, int T, int MODE, bool FAST>
+template <class Tr, int V, int NW, int T, int MODE, bool FAST>
 __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorMap* tmap_rho,
                                         const TBArgs& a, int bx, int by, int bz,
                                         unsigned char* smem, int* s_abort) {
@@ -112,8 +101,8 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
     using C = typename Tr::C;
     constexpr int NS = kRing;
     constexpr int NSR = rho_slots<MODE, NS, T>();
-    using L = TBLayout<V, NW, R, T, NS, S, NSR>;
-    constexpr int EX = L::EX, EY = L::EY, PLANE = L::PLANE, LPLANE = L::LPLANE;
+    using L = TBLayout<V, NW, T, NS, S, NSR>;
+    constexpr int EX = L::EX, EY = L::EY, PLANE = L::PLANE;
     constexpr uint32_t kPlaneBytes = PLANE * sizeof(S);
     // bytes landing per ring slot: the grid plane, and the rho plane of the same k
     constexpr uint32_t kSlotBytes = (NSR > 0 ? 2 : 1) * kPlaneBytes;
@@ -134,30 +123,20 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
     const int kz1 = min(g.nz + 1, kz0 + a.kz);
     const int Zlo = kz0 - T;
     const int M = (kz1 - kz0) + 2 * T;
-    const int row0 = w * R;            // first tile row of this thread's strip
-    const int gy0 = Y0 + row0;
+    const int gy = Y0 + w;
     const int gx0 = X0 + lane * V;
-    // deepest level any row of the strip takes part in
-    int smax = 0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) smax = max(smax, min(row0 + r, EY - 1 - row0 - r));
+    const int smax = min(w, EY - 1 - w);  // deepest level this warp's row takes part in
 
-    bool inxy[R][V], outxy[R][V], all_out[R], all_in[R];
+    bool inxy[V], outxy[V];
+    bool all_out = true, all_in = true;
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int gy = gy0 + r;
-        all_out[r] = true;
-        all_in[r] = true;
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-            const int x = gx0 + e;
-            inxy[r][e] = FAST || ((x >= 1) && (x <= g.nx) && (gy >= 1) && (gy <= g.ny));
-            outxy[r][e] = inxy[r][e] && (x >= ox0) && (x < ox0 + a.ox) && (x <= g.nx) &&
-                          (gy >= oy0) && (gy < oy0 + OY) && (gy <= g.ny) && (x >= 1) &&
-                          (gy >= 1);
-            all_out[r] = all_out[r] && outxy[r][e];
-            all_in[r] = all_in[r] && inxy[r][e];
-        }
+    for (int e = 0; e < V; ++e) {
+        const int x = gx0 + e;
+        inxy[e] = FAST || ((x >= 1) && (x <= g.nx) && (gy >= 1) && (gy <= g.ny));
+        outxy[e] = inxy[e] && (x >= ox0) && (x < ox0 + a.ox) && (x <= g.nx) && (gy >= oy0) &&
+                   (gy < oy0 + OY) && (gy <= g.ny) && (x >= 1) && (gy >= 1);
+        all_out = all_out && outxy[e];
+        all_in = all_in && inxy[e];
     }
 
     if (tid == 0) {
@@ -179,71 +158,58 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
         rslot = issued;  // NS < NSR
     }
 
-    C rr[T][3][R][V];  // per level s < T: 3 planes (roles rotate with the step) of level s
+    C r[T][3][V];                                 // per level s < T: 3 planes of level s
 #pragma unroll
     for (int s = 0; s < T; ++s)
 #pragma unroll
         for (int j = 0; j < 3; ++j)
 #pragma unroll
-            for (int r = 0; r < R; ++r)
-#pragma unroll
-                for (int e = 0; e < V; ++e) rr[s][j][r][e] = C(0);
+            for (int e = 0; e < V; ++e) r[s][j][e] = C(0);
 
     const C c6 = Tr::sixth();
     S* dst = static_cast<S*>(a.dst);
     S* grad = static_cast<S*>(a.grad);
-    const long long rowoff0 = (long long)gy0 * g.px + gx0;  // valid only when used
-    const int mycol = lane * V;
-    // shared-memory rows: the strip's edges in a level buffer, and its neighbours
-    const int lrow_top = (R == 1) ? w : 2 * w;
-    const int lrow_bot = (R == 1) ? w : 2 * w + 1;
-    const int lrow_above = lrow_top - 1, lrow_below = lrow_bot + 1;
-    const int prow_above = row0 - 1, prow_below = row0 + R;
-
-    // boundary-gradient accumulation (MODE_ADJ): face flags per cell, 5 bits each
-    // (x = 1, x = nx, y = 1, y = ny, owned), precomputed; z faces are uniform per plane
-    unsigned long long fmask = 0;
-    bool xy_face = false;
+    const long long rowoff = (long long)gy * g.px + gx0;  // valid only when used
+    const int mycol = w * EX + lane * V;
+    // boundary-gradient accumulation (MODE_ADJ): face flags per cell, 4 bits each
+    // (x = 1, x = nx, y = 1, y = ny), precomputed; z faces are uniform per plane
+    uint32_t fmask = 0;
     if (MODE == MODE_ADJ) {
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int e = 0; e < V; ++e) {
-                const int x = gx0 + e, gy = gy0 + r;
-                unsigned long long f = 0;
-                if (outxy[r][e])
-                    f = ((x == 1) ? 1u : 0u) | ((x == g.nx) ? 2u : 0u) | ((gy == 1) ? 4u : 0u) |
-                        ((gy == g.ny) ? 8u : 0u) | 16u;
-                fmask |= f << (5 * (r * V + e));
-                xy_face = xy_face || (f & 15u);
-            }
+        for (int e = 0; e < V; ++e) {
+            const int x = gx0 + e;
+            if (outxy[e])
+                fmask |= ((x == 1) ? 1u : 0u) | ((x == g.nx) ? 2u : 0u) | ((gy == 1) ? 4u : 0u) |
+                         ((gy == g.ny) ? 8u : 0u) | 16u;  // 16: cell owned (z faces)
+            if (e + 1 < V) fmask <<= 5;
+        }
     }
-    auto adj_acc = [&](const C (&v)[R][V], int p) {
+    constexpr uint32_t kXYFaces = 0x1EF7BDEFu & ((V >= 6) ? 0xFFFFFFFFu : ((1u << (5 * V)) - 1u));
+    const bool xy_face = (fmask & kXYFaces) != 0u;  // this thread owns an x or y face cell
+    auto adj_acc = [&](const C* v, int p) {
         if constexpr (MODE != MODE_ADJ || !std::is_same<S, C>::value) return;
         const bool zlo = p == 1, zhi = p == g.nz;
         // tiles inside the interior in x and y own no x/y face: only the z faces
         if (FAST ? !(zlo || zhi) : (!xy_face && !(zlo || zhi))) return;
-        if (p < kz0 || p >= kz1 || fmask == 0ull) return;
+        if (p < kz0 || p >= kz1 || fmask == 0u) return;
         C* gacc = reinterpret_cast<C*>(grad);  // the adjoint runs on FP32/FP64 grids
 #pragma unroll
-        for (int r = 0; r < R; ++r)
-#pragma unroll
-            for (int e = 0; e < V; ++e) {
-                const uint32_t f = (uint32_t)(fmask >> (5 * (r * V + e))) & 31u;
-                if (!(f & 16u)) continue;
-                const C cv = Tr::mul(c6, v[r][e]);
-                const int x = gx0 + e, gy = gy0 + r;
-                // fire-and-forget reductions: one thread owns each face cell and
-                // issues its contributions in level order, so the rounding sequence
-                // is that of grad += c*lambda_S, += c*lambda_{S-1}, ...
-                // (deterministic) without waiting for a read-modify-write
-                if (f & 1u) atomicAdd(gacc + g.lin(0, gy, p), cv);
-                if (f & 2u) atomicAdd(gacc + g.lin(g.nx + 1, gy, p), cv);
-                if (f & 4u) atomicAdd(gacc + g.lin(x, 0, p), cv);
-                if (f & 8u) atomicAdd(gacc + g.lin(x, g.ny + 1, p), cv);
-                if (zlo) atomicAdd(gacc + g.lin(x, gy, 0), cv);
-                if (zhi) atomicAdd(gacc + g.lin(x, gy, g.nz + 1), cv);
-            }
+        for (int e = 0; e < V; ++e) {
+            const uint32_t f = (fmask >> (5 * (V - 1 - e))) & 31u;
+            if (!(f & 16u)) continue;
+            const C cv = Tr::mul(c6, v[e]);
+            const int x = gx0 + e;
+            // fire-and-forget reductions: one thread owns each face cell and issues
+            // its contributions in level order, so the rounding sequence is that of
+            // grad += c*lambda_S, += c*lambda_{S-1}, ... (deterministic) without the
+            // warp waiting for a read-modify-write round trip
+            if (f & 1u) atomicAdd(gacc + g.lin(0, gy, p), cv);
+            if (f & 2u) atomicAdd(gacc + g.lin(g.nx + 1, gy, p), cv);
+            if (f & 4u) atomicAdd(gacc + g.lin(x, 0, p), cv);
+            if (f & 8u) atomicAdd(gacc + g.lin(x, g.ny + 1, p), cv);
+            if (zlo) atomicAdd(gacc + g.lin(x, gy, 0), cv);
+            if (zhi) atomicAdd(gacc + g.lin(x, gy, g.nz + 1), cv);
+        }
     };
 
     int cur_m = 0;  // step being executed (for the clean-up after a timeout)
@@ -263,108 +229,76 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
         // ---- level 0: plane Zlo + m, own cells
         const int p0 = Zlo + m;
         {
+            const Vec<S, V> t = *reinterpret_cast<const Vec<S, V>*>(ring + SLOT * PLANE + mycol);
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const Vec<S, V> t = *reinterpret_cast<const Vec<S, V>*>(
-                    ring + SLOT * PLANE + (row0 + r) * EX + mycol);
-#pragma unroll
-                for (int e = 0; e < V; ++e) rr[0][NEW][r][e] = Tr::ld(t.v[e]);
-            }
-            if (MODE == MODE_ADJ) adj_acc(rr[0][NEW], p0);
+            for (int e = 0; e < V; ++e) r[0][NEW][e] = Tr::ld(t.v[e]);
+            if (MODE == MODE_ADJ) adj_acc(r[0][NEW], p0);
         }
         // ---- levels 1..T
 #pragma unroll
         for (int s = 1; s <= T; ++s) {
             if (m < s) continue;     // pipeline fill
-            if (s > smax) continue;  // the whole strip is outside level s's region
+            if (s > smax) continue;  // row outside level s's region
             const int q = p0 - s;
             const bool zin = (q >= 1) && (q <= g.nz);
-            // rows just above and below the strip, level s-1, plane q
-            Vec<S, V> vn, vs;
-            if (s == 1) {
-                vn = *reinterpret_cast<const Vec<S, V>*>(ring + PSLOT * PLANE +
-                                                         prow_above * EX + mycol);
-                vs = *reinterpret_cast<const Vec<S, V>*>(ring + PSLOT * PLANE +
-                                                         prow_below * EX + mycol);
-            } else {
-                const S* nb = lvl + ((s - 2) * 2 + (PAR ^ 1)) * LPLANE;
-                vn = *reinterpret_cast<const Vec<S, V>*>(nb + lrow_above * EX + mycol);
-                vs = *reinterpret_cast<const Vec<S, V>*>(nb + lrow_below * EX + mycol);
-            }
-            // rho at plane q (MODE_RHS): rho slot of relative plane m - s
-            Vec<S, V> vr[R];
+            const S* nb = (s == 1) ? ring + PSLOT * PLANE
+                                   : lvl + ((s - 2) * 2 + (PAR ^ 1)) * PLANE;
+            const Vec<S, V> vn = *reinterpret_cast<const Vec<S, V>*>(nb + mycol - EX);
+            const Vec<S, V> vs = *reinterpret_cast<const Vec<S, V>*>(nb + mycol + EX);
+            // rho at plane q (MODE_RHS): the rho slot of plane Zlo + m - s
+            Vec<S, V> vr;
             if (MODE == MODE_RHS) {
                 const int sl = (rs >= s) ? rs - s : rs - s + (NSR > 0 ? NSR : 1);
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    vr[r] = *reinterpret_cast<const Vec<S, V>*>(rring + sl * PLANE +
-                                                                (row0 + r) * EX + mycol);
+                vr = *reinterpret_cast<const Vec<S, V>*>(rring + sl * PLANE + mycol);
             }
-            C out[R][V];
+            const C left = __shfl_up_sync(FULL, r[s - 1][CUR][V - 1], 1);
+            const C right = __shfl_down_sync(FULL, r[s - 1][CUR][0], 1);
+            C out[V];
+            if (zin) {
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                const C left = __shfl_up_sync(FULL, rr[s - 1][CUR][r][V - 1], 1);
-                const C right = __shfl_down_sync(FULL, rr[s - 1][CUR][r][0], 1);
-                if (zin) {
-#pragma unroll
-                    for (int e = 0; e < V; ++e) {
-                        const C l = (e == 0) ? left : rr[s - 1][CUR][r][e - 1];
-                        const C rt = (e == V - 1) ? right : rr[s - 1][CUR][r][e + 1];
-                        const C nn = (r == 0) ? Tr::ld(vn.v[e]) : rr[s - 1][CUR][r - 1][e];
-                        const C ss =
-                            (r == R - 1) ? Tr::ld(vs.v[e]) : rr[s - 1][CUR][(r + 1) % R][e];
-                        C sum = Tr::add(l, rt);
-                        sum = Tr::add(sum, nn);
-                        sum = Tr::add(sum, ss);
-                        sum = Tr::add(sum, rr[s - 1][OLD][r][e]);
-                        sum = Tr::add(sum, rr[s - 1][NEW][r][e]);
-                        if (MODE == MODE_RHS) sum = Tr::add(sum, Tr::ld(vr[r].v[e]));
-                        const C val = Tr::rnd(Tr::mul(sum, c6));
-                        out[r][e] = (FAST || inxy[r][e]) ? val : rr[s - 1][CUR][r][e];
-                    }
-                } else {
-#pragma unroll
-                    for (int e = 0; e < V; ++e) out[r][e] = rr[s - 1][CUR][r][e];
+                for (int e = 0; e < V; ++e) {
+                    const C l = (e == 0) ? left : r[s - 1][CUR][e - 1];
+                    const C rr = (e == V - 1) ? right : r[s - 1][CUR][e + 1];
+                    C sum = Tr::add(l, rr);
+                    sum = Tr::add(sum, Tr::ld(vn.v[e]));
+                    sum = Tr::add(sum, Tr::ld(vs.v[e]));
+                    sum = Tr::add(sum, r[s - 1][OLD][e]);
+                    sum = Tr::add(sum, r[s - 1][NEW][e]);
+                    if (MODE == MODE_RHS) sum = Tr::add(sum, Tr::ld(vr.v[e]));
+                    const C val = Tr::rnd(Tr::mul(sum, c6));
+                    out[e] = (FAST || inxy[e]) ? val : r[s - 1][CUR][e];
                 }
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) out[e] = r[s - 1][CUR][e];
             }
             if (s < T) {
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-#pragma unroll
-                    for (int e = 0; e < V; ++e) rr[s < T ? s : 0][NEW][r][e] = out[r][e];
-                S* lb = lvl + ((s - 1) * 2 + PAR) * LPLANE;
                 Vec<S, V> o;
 #pragma unroll
-                for (int e = 0; e < V; ++e) o.v[e] = Tr::st(out[0][e]);
-                *reinterpret_cast<Vec<S, V>*>(lb + lrow_top * EX + mycol) = o;
-                if (R > 1) {
-#pragma unroll
-                    for (int e = 0; e < V; ++e) o.v[e] = Tr::st(out[R - 1][e]);
-                    *reinterpret_cast<Vec<S, V>*>(lb + lrow_bot * EX + mycol) = o;
+                for (int e = 0; e < V; ++e) {
+                    r[s < T ? s : 0][NEW][e] = out[e];
+                    o.v[e] = Tr::st(out[e]);
                 }
+                *reinterpret_cast<Vec<S, V>*>(lvl + ((s - 1) * 2 + PAR) * PLANE + mycol) = o;
                 if (MODE == MODE_ADJ) adj_acc(out, q);
             } else if (q >= kz0 && q < kz1) {
+                const long long o = g.plane * q + rowoff;
+                if (all_out) {
+                    Vec<S, V> ov;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const long long o = g.plane * q + rowoff0 + (long long)r * g.px;
-                    if (all_out[r]) {
-                        Vec<S, V> ov;
+                    for (int e = 0; e < V; ++e) ov.v[e] = Tr::st(out[e]);
+                    *reinterpret_cast<Vec<S, V>*>(dst + o) = ov;
+                } else {
 #pragma unroll
-                        for (int e = 0; e < V; ++e) ov.v[e] = Tr::st(out[r][e]);
-                        *reinterpret_cast<Vec<S, V>*>(dst + o) = ov;
-                    } else {
-#pragma unroll
-                        for (int e = 0; e < V; ++e)
-                            if (outxy[r][e]) dst[o + e] = Tr::st(out[r][e]);
-                    }
+                    for (int e = 0; e < V; ++e)
+                        if (outxy[e]) dst[o + e] = Tr::st(out[e]);
                 }
             }
         }
         __syncthreads();
         if (*s_abort) return false;
-        // the slot of plane Zlo+m-1 is free now: refill it with plane Zlo+m-1+NS
-        // (and the rho plane of that k into the rho slot whose last reader, level
-        // T at step m-NS+... , has finished: see rho_slots)
+        // the slot of plane Zlo+m-1 is free now: refill it with plane Zlo+m-1+NS,
+        // and the rho ring's next slot with rho of the same k (see rho_slots)
         if (tid == 0 && m >= 1 && issued < M) {
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(&bars[PSLOT], kSlotBytes);
@@ -415,16 +349,15 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
 }
 
 // CTA-uniform test: the extended tile lies inside the interior in x and y.
-template <int V, int NW, int R, int T>
+template <int V, int NW, int T>
 __device__ __forceinline__ bool tile_inside_xy(const TBArgs& a, int bx, int by) {
-    constexpr int EY = NW * R;
     const int X0 = a.x0_first + bx * a.ox;
-    const int Y0 = 1 - T + by * (EY - 2 * T);
-    return X0 >= 1 && X0 + 32 * V - 1 <= a.g.nx && Y0 >= 1 && Y0 + EY - 1 <= a.g.ny;
+    const int Y0 = 1 - T + by * (NW - 2 * T);
+    return X0 >= 1 && X0 + 32 * V - 1 <= a.g.nx && Y0 >= 1 && Y0 + NW - 1 <= a.g.ny;
 }
 
-template <class Tr, int V, int NW, int R, int T, int MODE, int NS, int MINB>
-__global__ void __launch_bounds__(NW * 32, MINB)
+template <class Tr, int V, int NW, int T, int MODE, int NS>
+__global__ void __launch_bounds__(NW * 32, 1)
     tb_sweep_kernel(const __grid_constant__ CUtensorMap tmap,
                     const __grid_constant__ CUtensorMap tmap_rho, const TBArgs a) {
     static_assert(NS == kRing, "the k-march is unrolled by the ring size");
@@ -436,10 +369,10 @@ __global__ void __launch_bounds__(NW * 32, MINB)
         if (MODE == MODE_RHS) prefetch_tmap(&tmap_rho);
     }
     const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
-    if (tile_inside_xy<V, NW, R, T>(a, bx, by))
-        tb_tile<Tr, V, NW, R, T, MODE, true>(&tmap, &tmap_rho, a, bx, by, bz, smem, &s_abort);
+    if (tile_inside_xy<V, NW, T>(a, bx, by))
+        tb_tile<Tr, V, NW, T, MODE, true>(&tmap, &tmap_rho, a, bx, by, bz, smem, &s_abort);
     else
-        tb_tile<Tr, V, NW, R, T, MODE, false>(&tmap, &tmap_rho, a, bx, by, bz, smem, &s_abort);
+        tb_tile<Tr, V, NW, T, MODE, false>(&tmap, &tmap_rho, a, bx, by, bz, smem, &s_abort);
 }
 
 }  // namespace jac

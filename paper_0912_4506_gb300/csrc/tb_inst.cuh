@@ -7,17 +7,16 @@
 
 namespace jac {
 
-template <class TR, int V, int NW, int R, int T, int MODE, int NS>
+template <class TR, int V, int NW, int T, int MODE, int NS>
 constexpr size_t tb_smem_bytes() {
-    return TBLayout<V, NW, R, T, NS, typename TR::S, rho_slots<MODE, NS, T>()>::bytes();
+    return TBLayout<V, NW, T, NS, typename TR::S, rho_slots<MODE, NS, T>()>::bytes();
 }
 
-template <class TR, int V, int NW, int R, int T, int MODE, int NS, int MINB>
+template <class TR, int V, int NW, int T, int MODE, int NS>
 cudaError_t tb_launch(const CUtensorMap& map, const CUtensorMap& map_rho, const TBArgs& a,
                       dim3 grid, cudaStream_t st) {
-    constexpr size_t smem = tb_smem_bytes<TR, V, NW, R, T, MODE, NS>();
-    tb_sweep_kernel<TR, V, NW, R, T, MODE, NS, MINB><<<grid, NW * 32, smem, st>>>(map, map_rho,
-                                                                                 a);
+    constexpr size_t smem = tb_smem_bytes<TR, V, NW, T, MODE, NS>();
+    tb_sweep_kernel<TR, V, NW, T, MODE, NS><<<grid, NW * 32, smem, st>>>(map, map_rho, a);
     return cudaGetLastError();
 }
 
@@ -32,14 +31,10 @@ cudaError_t plain_launch(const void* A, void* B, const Geom& g, int kchunk, dim3
 
 }  // namespace jac
 
-// MINB: CTAs per SM the register allocation must allow (__launch_bounds__)
-#define JAC_TBM(TR, V, NW, R, T, MODE, NS, MINB)                                          \
-    {TR::kDtype, MODE, V, NW, R, T, NS, MINB,                                             \
-     ::jac::tb_smem_bytes<TR, V, NW, R, T, MODE, NS>(),                                   \
-     &::jac::tb_launch<TR, V, NW, R, T, MODE, NS, MINB>,                                  \
-     reinterpret_cast<const void*>(&::jac::tb_sweep_kernel<TR, V, NW, R, T, MODE, NS, MINB>)}
-#define JAC_TBR(TR, V, NW, R, T, MODE, NS) JAC_TBM(TR, V, NW, R, T, MODE, NS, 1)
-#define JAC_TB(TR, V, NW, T, MODE, NS) JAC_TBR(TR, V, NW, 1, T, MODE, NS)
+#define JAC_TB(TR, V, NW, T, MODE, NS)                                         \
+    {TR::kDtype, MODE, V, NW, T, NS, ::jac::tb_smem_bytes<TR, V, NW, T, MODE, NS>(), \
+     &::jac::tb_launch<TR, V, NW, T, MODE, NS>,                               \
+     reinterpret_cast<const void*>(&::jac::tb_sweep_kernel<TR, V, NW, T, MODE, NS>)}
 
 #define JAC_PLAIN(TR, V, WY, NEMU) \
     {TR::kDtype, V, WY, NEMU, &::jac::plain_launch<TR, V, WY, NEMU>, \

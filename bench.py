@@ -64,7 +64,8 @@ def parse():
     p.add_argument("--no-variants", action="store_true", help="skip the extra rows")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--case", default="", help="profiling case: run only one kernel "
-                   "configuration, e.g. --case sweep --dtype f32 --kernel tb --t 4 --size 384")
+                   "configuration, e.g. --case sweep --dtype f32 --kernel tb --t 4 --size 384 "
+                   "(cases: sweep, rhs, residual, adjoint)")
     p.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
     p.add_argument("--kernel", default="auto", choices=["auto", "plain", "tb"])
     p.add_argument("--size", type=int, default=NX)
@@ -626,6 +627,31 @@ def run_case(args):
         return
     a = inputs.to_dtype(inputs.uniform_grid_f64(n, n, n), args.dtype,
                         px=inputs.row_pitch(n, args.dtype))
+    if args.case == "rhs":
+        # correction sweeps: e = uniform interior (zero boundary), rho = 0.1 * same
+        e = api.from_numpy(a, n, "cuda")
+        for sl in (e[0], e[-1], e[:, 0], e[:, -1], e[:, :, 0], e[:, :, n + 1]):
+            sl.zero_()
+        rho = api.alloc_like(e)
+        rho.copy_(e * 0.1)
+        j = api.Jacobi(e)
+        for _ in range(args.warmup):
+            j.sweep_rhs(rho, args.sweeps, args.t)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            j.sweep_rhs(rho, args.sweeps, args.t)
+        e1.record()
+        torch.cuda.synchronize()
+        j.check()
+        ms = e0.elapsed_time(e1) / args.steps
+        print(json.dumps({"case": "rhs", "dtype": args.dtype, "t": args.t, "size": n,
+                          "sweeps": args.sweeps, "ms": round(ms, 4),
+                          "glups": round(n ** 3 * args.sweeps / ms / 1e6, 2)}), flush=True)
+        j.close()
+        return
     j = api.Jacobi(api.from_numpy(a, n, "cuda"))
     kern = {"auto": api.JAC_KERNEL_AUTO, "plain": api.JAC_KERNEL_PLAIN,
             "tb": api.JAC_KERNEL_TB}[args.kernel]

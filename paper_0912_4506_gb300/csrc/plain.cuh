@@ -15,101 +15,79 @@
 
 namespace jac {
 
+// The sweep of one chunk for FP32/bf16 storage (arithmetic in FP32, Eq. 1's
+// operand order).  The sweep is bound by HBM, so the march keeps several planes of
+// loads in flight and spends few instructions per step: one base pointer at plane
+// k+1 advances by a plane per step, and every load is that pointer plus a row,
+// plane or element offset (the stream of plane k+3, the rows above and below of
+// plane k+1, the two x-edge cells of plane k+1); values stay in storage format
+// until used.  Loads past the last plane of the array are skipped (the stream
+// runs ahead of the chunk by two planes).
 template <class Tr, int V>
-__device__ __forceinline__ void load_vec(const typename Tr::S* __restrict__ p, bool ok,
-                                         typename Tr::C (&out)[V]) {
-    using S = typename Tr::S;
-    if (ok) {
-        const Vec<S, V> t = ldg_vec<S, V>(p);
-#pragma unroll
-        for (int e = 0; e < V; ++e) out[e] = Tr::ld(t.v[e]);
-    } else {
-#pragma unroll
-        for (int e = 0; e < V; ++e) out[e] = 0;
-    }
-}
-
-// The sweep of one chunk, with the first NEMU of the five additions done by
-// add_pos_exact (FP64 only; NEMU = 0: all on the FP64 unit).  NEMU is counted in
-// half additions: an odd NEMU does NEMU/2 on even planes and NEMU/2 + 1 on odd
-// planes, which balances the FP64 and integer pipes between whole splits.
-// Software-pipelined: while plane k is computed, plane k+3 (the stream from HBM)
-// and the in-plane neighbours of plane k+1 are already being loaded, so each
-// thread keeps two steps of loads in flight.
-template <class Tr, int V, int NEMU>
 __device__ __forceinline__ void plain_march(const typename Tr::S* __restrict__ A,
                                             typename Tr::S* __restrict__ B, const Geom& g,
-                                            int k0, int k1, int x0, int y, int lane,
-                                            bool loadable, const bool (&interior)[V],
-                                            bool all_interior, bool left_ok, bool right_ok,
-                                            long long row) {
+                                            int k0, int k1, int lane, bool loadable,
+                                            const bool (&interior)[V], bool all_interior,
+                                            bool left_ok, bool right_ok, long long row) {
     using S = typename Tr::S;
     using C = typename Tr::C;
+    using VS = Vec<S, V>;
     const unsigned FULL = 0xffffffffu;
     const C c6 = Tr::sixth();
-    auto add = [](int idx, int nemu, C a, C b) -> C {
-        if constexpr (NEMU > 0) {
-            if (idx < nemu) return add_pos_exact(a, b);
-        }
-        return Tr::add(a, b);
-    };
+    const long long plane = g.plane, px = g.px;
     const int ktop = g.nz + 1;  // last plane in the array
-    auto edge_l = [&](int k) -> C {
-        return (lane == 0 && left_ok) ? Tr::ld(__ldg(A + row + g.plane * k - 1)) : C(0);
-    };
-    auto edge_r = [&](int k) -> C {
-        return (lane == 31 && right_ok) ? Tr::ld(__ldg(A + row + g.plane * k + V)) : C(0);
-    };
-
-    // streamed values are kept in storage format (bf16 stays 16-bit) and
-    // converted when used
-    using VS = Vec<S, V>;
-    auto ldv = [&](long long off) -> VS {
-        if (loadable) return ldg_vec<S, V>(A + off);
-        VS z;
+    const bool el_ok = lane == 0 && left_ok, er_ok = lane == 31 && right_ok;
+    VS zero;
 #pragma unroll
-        for (int e = 0; e < V; ++e) z.v[e] = S(0);
-        return z;
-    };
-    VS dn = ldv(row + g.plane * (k0 - 1));
-    VS ct = ldv(row + g.plane * k0);
-    VS up = ldv(row + g.plane * min(k0 + 1, ktop));
-    VS up2 = ldv(row + g.plane * min(k0 + 2, ktop));
-    VS no = ldv(row + g.plane * k0 - g.px);
-    VS so = ldv(row + g.plane * k0 + g.px);
-    C el = edge_l(k0), er = edge_r(k0);
+    for (int e = 0; e < V; ++e) zero.v[e] = S(0);
+    auto ldv = [&](const S* p, bool ok) -> VS { return ok ? ldg_vec<S, V>(p) : zero; };
+    auto lds = [&](const S* p, bool ok) -> S { return ok ? __ldg(p) : S(0); };
 
-    auto plane_step = [&](int k, int nemu) {
-        // loads for the next steps first
-        const int kn = min(k + 1, ktop);
-        const VS up3 = ldv(row + g.plane * min(k + 3, ktop));
-        const VS no2 = ldv(row + g.plane * kn - g.px);
-        const VS so2 = ldv(row + g.plane * kn + g.px);
-        const C el2 = edge_l(kn), er2 = edge_r(kn);
+    // p1: (x0, y) of plane k+1 in A; planes k0-1 .. k0+2 and the in-plane
+    // neighbours of plane k0 are loaded before the march
+    const S* p1 = A + row + plane * k0;
+    VS dn = ldv(p1 - plane, loadable);
+    VS ct = ldv(p1, loadable);
+    VS up = ldv(p1 + plane, loadable && k0 + 1 <= ktop);
+    VS up2 = ldv(p1 + 2 * plane, loadable && k0 + 2 <= ktop);
+    VS no = ldv(p1 - px, loadable);
+    VS so = ldv(p1 + px, loadable);
+    S el = lds(p1 - 1, el_ok), er = lds(p1 + V, er_ok);
+    p1 += plane;
+    S* pb = B + row + plane * k0;
+
+#pragma unroll 2
+    for (int k = k0; k <= k1; ++k) {
+        // loads for the next steps first: stream plane k+3, neighbours of k+1
+        const VS up3 = ldv(p1 + 2 * plane, loadable && k + 3 <= ktop);
+        const bool n1 = loadable && k + 1 <= ktop;
+        const VS no2 = ldv(p1 - px, n1);
+        const VS so2 = ldv(p1 + px, n1);
+        const S el2 = lds(p1 - 1, el_ok && k + 1 <= ktop);
+        const S er2 = lds(p1 + V, er_ok && k + 1 <= ktop);
 
         C left = __shfl_up_sync(FULL, Tr::ld(ct.v[V - 1]), 1);
         C right = __shfl_down_sync(FULL, Tr::ld(ct.v[0]), 1);
-        if (lane == 0) left = el;
-        if (lane == 31) right = er;
+        if (lane == 0) left = Tr::ld(el);
+        if (lane == 31) right = Tr::ld(er);
         VS outv;
 #pragma unroll
         for (int e = 0; e < V; ++e) {
             const C l = (e == 0) ? left : Tr::ld(ct.v[e - 1]);
             const C r = (e == V - 1) ? right : Tr::ld(ct.v[e + 1]);
-            C s = add(0, nemu, l, r);
-            s = add(1, nemu, s, Tr::ld(no.v[e]));
-            s = add(2, nemu, s, Tr::ld(so.v[e]));
-            s = add(3, nemu, s, Tr::ld(dn.v[e]));
-            s = add(4, nemu, s, Tr::ld(up.v[e]));
+            C s = Tr::add(l, r);
+            s = Tr::add(s, Tr::ld(no.v[e]));
+            s = Tr::add(s, Tr::ld(so.v[e]));
+            s = Tr::add(s, Tr::ld(dn.v[e]));
+            s = Tr::add(s, Tr::ld(up.v[e]));
             outv.v[e] = Tr::st(Tr::mul(s, c6));
         }
-        const long long base = row + g.plane * k;
         if (all_interior) {
-            *reinterpret_cast<VS*>(B + base) = outv;
+            *reinterpret_cast<VS*>(pb) = outv;
         } else {
 #pragma unroll
             for (int e = 0; e < V; ++e)
-                if (interior[e]) B[base + e] = outv.v[e];
+                if (interior[e]) pb[e] = outv.v[e];
         }
         dn = ct;
         ct = up;
@@ -119,15 +97,9 @@ __device__ __forceinline__ void plain_march(const typename Tr::S* __restrict__ A
         so = so2;
         el = el2;
         er = er2;
-    };
-    constexpr int kEven = NEMU / 2, kOdd = (NEMU + 1) / 2;
-    int k = k0;
-#pragma unroll 1
-    for (; k + 1 <= k1; k += 2) {
-        plane_step(k, kEven);
-        plane_step(k + 1, kOdd);
+        p1 += plane;
+        pb += plane;
     }
-    if (k <= k1) plane_step(k, kEven);
 }
 
 // FP64 variant of the march.  The FP64 sweep is bound by its arithmetic pipes
@@ -249,8 +221,8 @@ __global__ void __launch_bounds__(32 * WY)
             plain_march_shallow<Tr, V, 0>(A, B, g, k0, k1, x0, y, lane, loadable, interior,
                                           all_interior, left_ok, right_ok, row, one);
     } else {
-        plain_march<Tr, V, 0>(A, B, g, k0, k1, x0, y, lane, loadable, interior, all_interior,
-                              left_ok, right_ok, row);
+        plain_march<Tr, V>(A, B, g, k0, k1, lane, loadable, interior, all_interior, left_ok,
+                           right_ok, row);
     }
 }
 

@@ -102,9 +102,11 @@ JAC_API int jacobi_create(jacobi_t *out, int nx, int ny, int nz, int dtype, void
 
 /*
  * jacobi_sweep — nsweeps sweeps of Eq. 1, A -> B -> A ... (Sect. 1.1).
- *   t          temporal-blocking depth request: 0 = planner's choice, 1 = plain
- *              streaming kernel, t >= 2 = passes of depth min(t, deepest feasible)
- *              with a shallower last pass when t does not divide nsweeps.
+ *   t          temporal-blocking depth request: 0 = planner's choice (FP64: 1,
+ *              FP32/bf16: 4), 1 = one sweep per pass (FP64: the register-march
+ *              streaming kernel; FP32/bf16: the TMA-ring kernel at depth 1),
+ *              t >= 2 = passes of depth min(t, deepest feasible) with a shallower
+ *              last pass when t does not divide nsweeps.
  *   final_is_b set to 1 when the result is in B, else 0.  Every pass (one plain
  *              sweep, or one blocked pass of several sweeps) reads one grid and
  *              writes the other, so this is the parity of the number of passes.
@@ -113,7 +115,8 @@ JAC_API int jacobi_create(jacobi_t *out, int nx, int ny, int nz, int dtype, void
 JAC_API int jacobi_sweep(jacobi_t h, int nsweeps, int t, int *final_is_b);
 
 /* jacobi_sweep_ex — as jacobi_sweep, with the kernel family forced
- * (JAC_KERNEL_TB with t == 1 runs the blocked kernel at depth 1). */
+ * (JAC_KERNEL_PLAIN: the register-march streaming kernel for every dtype;
+ * JAC_KERNEL_TB with t == 1 runs the blocked kernel at depth 1). */
 JAC_API int jacobi_sweep_ex(jacobi_t h, int nsweeps, int t, int kernel, int *final_is_b);
 
 /* jacobi_plan — fill *info with the plan jacobi_sweep_ex(h, nsweeps, t, kernel)

@@ -262,7 +262,11 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
     if (!h || nsweeps < 0 || t < 0) return JAC_EINVAL;
     if (kernel < JAC_KERNEL_AUTO || kernel > JAC_KERNEL_TB) return JAC_EINVAL;
     if (t == 0) t = default_t(h->dtype, mode);
-    if (kernel == JAC_KERNEL_AUTO) kernel = (t == 1) ? JAC_KERNEL_PLAIN : JAC_KERNEL_TB;
+    // depth 1: FP64 takes the register-march streaming kernel (FP64-pipe bound, with
+    // the integer-pipe additions); FP32/bf16 take the TMA-ring kernel at depth 1
+    // (128 x 12 tiles), which keeps more bytes in flight than the register march
+    if (kernel == JAC_KERNEL_AUTO)
+        kernel = (t == 1 && h->dtype == JAC_F64) ? JAC_KERNEL_PLAIN : JAC_KERNEL_TB;
     if (mode != MODE_PLAIN) kernel = JAC_KERNEL_TB;  // RHS/adjoint only exist blocked
     if (cudaSetDevice(h->device) != cudaSuccess) return JAC_ECUDA;
 

@@ -5,7 +5,7 @@
 namespace jac {
 
 static const TBEntry kTB[] = {
-    JAC_TB(BF16, 2, 32, 1, MODE_PLAIN, 6), JAC_TB(BF16, 2, 32, 2, MODE_PLAIN, 6),
+    JAC_TB(BF16, 4, 12, 1, MODE_PLAIN, 6), JAC_TB(BF16, 2, 32, 2, MODE_PLAIN, 6),
     JAC_TB(BF16, 2, 32, 3, MODE_PLAIN, 6), JAC_TB(BF16, 2, 32, 4, MODE_PLAIN, 6),
     JAC_TB(BF16, 2, 32, 5, MODE_PLAIN, 6), JAC_TB(BF16, 2, 32, 6, MODE_PLAIN, 6),
     JAC_TB(BF16, 2, 32, 7, MODE_PLAIN, 6), JAC_TB(BF16, 2, 32, 8, MODE_PLAIN, 6),

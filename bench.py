@@ -233,7 +233,7 @@ def variant_rows(dev, steps):
         j = api.Jacobi(api.from_numpy(make_input(dtype), NX, dev))
         tmax = 4 if dtype == "f64" else 8
         for t, kern, name in [(1, api.JAC_KERNEL_PLAIN, "plain")] + \
-                [(t, api.JAC_KERNEL_TB, f"tb_t{t}") for t in (1, 2, 4, 8, 16)
+                [(t, api.JAC_KERNEL_TB, f"tb_t{t}") for t in (1, 2, 3, 4, 8, 16)
                  if t <= tmax or dtype == "f64"]:
             ms = time_sweeps(j, NSWEEPS, t, kern, steps, 1, stream)
             plan = j.plan(NSWEEPS, t, kern)
@@ -247,7 +247,7 @@ def variant_rows(dev, steps):
     return rows
 
 
-def variant_precision(dev, n=1024, outer=20, inner=50, t=4):
+def variant_precision(dev, n=1024, outer=20, inner=50, t=(("f32", 4), ("bf16", 2))):
     """Laplace problem on an n^3 interior: FP64 reference = outer*inner plain FP64
     sweeps; FP32 and bf16 refinement (inner sweeps in low precision, FP64
     residual).  GLUP/s counts outer*inner sweeps over the total time including the
@@ -273,10 +273,11 @@ def variant_precision(dev, n=1024, outer=20, inner=50, t=4):
     u_init = inputs.laplace_boundary_torch(n, n, n, device=dev)
     for dtype in ("f32", "bf16"):
         r = api.Refiner(api.as_grid(u_init, n), dtype)
-        r.run(1, 2, t)  # warm-up (plans, descriptors)
+        td = dict(t)[dtype]
+        r.run(1, 2, td)  # warm-up (plans, descriptors)
         torch.cuda.synchronize()
         e0.record()
-        out = r.run(outer, inner, t)
+        out = r.run(outer, inner, td)
         e1.record()
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
@@ -284,7 +285,7 @@ def variant_precision(dev, n=1024, outer=20, inner=50, t=4):
         scale = float(ref_keep.abs().max())
         rows[f"{dtype}_refined"] = {
             "glups": round(n ** 3 * total / ms / 1e6, 2), "ms": round(ms, 1),
-            "outer": outer, "inner": inner, "t": t, "max_abs_err_vs_fp64": err,
+            "outer": outer, "inner": inner, "t": td, "max_abs_err_vs_fp64": err,
             "max_rel_err_vs_fp64": err / scale}
         r.close()
         del r, out
@@ -334,7 +335,7 @@ def variant_batched(dev):
             "depth_histogram": hist, "launches_per_run": 1}
 
 
-def variant_adjoint(dev, n=256, nsweeps=50, t_fwd=4, t_adj=(("f32", 4), ("f64", 1))):
+def variant_adjoint(dev, n=256, nsweeps=50, t_fwd=3, t_adj=(("f32", 4), ("f64", 1))):
     """256^3 FP32, 50 sweeps: forward (blocked), adjoint (blocked, with the boundary
     gradient), beside the plain FP32 sweep; error of the FP32 gradient against the
     FP64 adjoint of the same loss.  Depths: the fastest measured on GB300 for each

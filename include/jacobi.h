@@ -103,7 +103,7 @@ JAC_API int jacobi_create(jacobi_t *out, int nx, int ny, int nz, int dtype, void
 /*
  * jacobi_sweep — nsweeps sweeps of Eq. 1, A -> B -> A ... (Sect. 1.1).
  *   t          temporal-blocking depth request: 0 = planner's choice (FP64: 1,
- *              FP32/bf16: 4), 1 = one sweep per pass (FP64: the register-march
+ *              FP32/bf16: 3), 1 = one sweep per pass (FP64: the register-march
  *              streaming kernel; FP32/bf16: the TMA-ring kernel at depth 1),
  *              t >= 2 = passes of depth min(t, deepest feasible) with a shallower
  *              last pass when t does not divide nsweeps.
@@ -130,7 +130,7 @@ JAC_API int jacobi_plan(jacobi_t h, int nsweeps, int t, int kernel, jacobi_plan_
  * iteration of (I - J0) e = rho/6 with J0 the sweep of Eq. 1 on a zero
  * boundary.  rho: device grid of the handle's dtype and layout (read only).
  * dtype JAC_F32 or JAC_BF16 (JAC_EUNSUPPORTED otherwise).  t, final_is_b as in
- * jacobi_sweep.
+ * jacobi_sweep (t = 0: depth 4 for FP32, 2 for bf16).
  */
 JAC_API int jacobi_sweep_rhs(jacobi_t h, const void *rho, int nsweeps, int t,
                      int *final_is_b);

@@ -248,12 +248,16 @@ int check_grid_args(int nx, int ny, int nz, int dtype, long long pitch) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Depth used when the caller leaves it to the planner (t = 0): FP64 is bound by
-// the FP64 pipe, so blocking cannot help it (plain streaming kernel); FP32 and
-// bf16 sweeps of every kind run fastest at depth 4 on GB300 at 512^3.
+// Depth used when the caller leaves it to the planner (t = 0), the fastest
+// measured at 512^3 on GB300: FP64 is bound by the FP64 pipe, so blocking cannot
+// help it (plain streaming kernel); plain FP32/bf16 sweeps peak at depth 3
+// (128 x 32 tiles), FP32 correction sweeps at 4 (tied with 3), bf16 correction
+// sweeps at 2, adjoint sweeps at 4.
 int default_t(int dtype, int mode) {
-    (void)mode;
-    return dtype == JAC_F64 ? 1 : 4;
+    if (dtype == JAC_F64) return 1;
+    if (mode == MODE_PLAIN) return 3;
+    if (mode == MODE_RHS) return dtype == JAC_BF16 ? 2 : 4;
+    return 4;
 }
 
 // Run nsweeps of `mode` as a sequence of passes.  kernel: JAC_KERNEL_*.

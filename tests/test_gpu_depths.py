@@ -67,5 +67,5 @@ def test_plan_reports_default_depth():
     j = api.Jacobi(api.as_grid(to_dev(a, "f32"), 96))
     p = j.plan(13, 0, api.JAC_KERNEL_AUTO)
     j.close()
-    assert p["t"] == 4 and p["remainder_t"] == 1 and p["passes"] == 4
+    assert p["t"] == 3 and p["remainder_t"] == 1 and p["passes"] == 5
     assert p["threads"] == 32 * p["ext_y"]

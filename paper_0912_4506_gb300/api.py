@@ -87,7 +87,9 @@ class Jacobi:
     A's layout if not given) receives A's boundary layer at construction.
     """
 
-    def __init__(self, A, B=None):
+    def __init__(self, A, B=None, stream=None):
+        """``stream``: the torch stream the handle launches on (default: the
+        current stream at construction)."""
         nx, ny, nz, px = grid_geom(A)
         self.nx, self.ny, self.nz, self.px = nx, ny, nz, px
         self.A = A
@@ -97,8 +99,9 @@ class Jacobi:
         self.dtype = _DT[A.dtype]
         self.device = A.device
         with torch.cuda.device(self.device):
+            sp = _stream_ptr(self.device) if stream is None else stream.cuda_stream
             self._h = _lib.jacobi_create(nx, ny, nz, self.dtype, A.data_ptr(),
-                                         self.B.data_ptr(), px, _stream_ptr(self.device))
+                                         self.B.data_ptr(), px, sp)
 
     # ------------------------------------------------------------------
     def sweep(self, nsweeps, t=0, kernel=JAC_KERNEL_AUTO):
@@ -164,6 +167,42 @@ class Jacobi:
         except Exception:
             pass
 
+
+
+class HostPipeline:
+    """End-to-end sweeps of independent problems held in (pinned) host memory.
+
+    Problem i is uploaded, swept and downloaded through handle i % 2; each handle
+    owns a device grid pair and launches on its own stream, so one problem's
+    host<->device copies overlap the other problem's sweeps (the host link, about
+    200 GB/s each way on GB300, is otherwise idle while the sweeps run)."""
+
+    def __init__(self, nx, ny, nz, dtype="f64", device="cuda"):
+        self.device = torch.device(device)
+        self.streams = [torch.cuda.Stream(self.device) for _ in range(2)]
+        self.jobs = []
+        for st in self.streams:
+            with torch.cuda.stream(st):
+                self.jobs.append(Jacobi(alloc_grid(nx, ny, nz, dtype, self.device),
+                                        stream=st))
+
+    def run(self, host_ins, host_outs, nsweeps, t=0, kernel=JAC_KERNEL_AUTO):
+        """Enqueue problem i (host_ins[i] -> host_outs[i]) on handle i % 2.  The
+        current stream waits for all of them; synchronise it before reading
+        host_outs.  Buffers of problems i and i + 1 must be distinct."""
+        with torch.cuda.device(self.device):
+            cur = torch.cuda.current_stream(self.device)
+            for st in self.streams:
+                st.wait_stream(cur)
+            for i, (hi, ho) in enumerate(zip(host_ins, host_outs)):
+                self.jobs[i % 2].run_host(hi, ho, nsweeps, t, kernel)
+            for st in self.streams:
+                cur.wait_stream(st)
+
+    def close(self):
+        for j in self.jobs:
+            j.close()
+        self.jobs = []
 
 def sweep(A, nsweeps, t=0, kernel=JAC_KERNEL_AUTO):
     """``nsweeps`` Jacobi sweeps of the grid ``A`` (not modified); returns a new

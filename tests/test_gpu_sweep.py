@@ -135,3 +135,22 @@ def test_full_size_512cubed_fp64(t, kernel):
     a, want = _oracle_512()
     got = run_gpu(a, 100, t, kernel, "f64", 512)
     assert first_diff(got, want) is None, (t, first_diff(got, want))
+
+
+def test_host_pipeline_matches_oracle():
+    """Independent problems through the two-handle host pipeline (copies of one
+    problem overlapping the sweeps of the next): each result equals the oracle's."""
+    import torch
+    from paper_0912_4506_gb300 import api, inputs
+    nx, ny, nz, n = 45, 38, 21, 7
+    px = inputs.row_pitch(nx, "f64")
+    probs = [inputs.uniform_grid_f64(nx, ny, nz, g=g, px=px) for g in range(5)]
+    ins = [torch.from_numpy(p).pin_memory() for p in probs]
+    outs = [torch.empty_like(x).pin_memory() for x in ins]
+    pipe = api.HostPipeline(nx, ny, nz, "f64")
+    pipe.run(ins, outs, n)
+    torch.cuda.synchronize()
+    pipe.close()
+    for p, o in zip(probs, outs):
+        want = oracle.sweeps(p, n, nx=nx)
+        assert np.array_equal(o.numpy()[:, :, :nx + 2], want[:, :, :nx + 2])

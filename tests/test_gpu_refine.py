@@ -53,6 +53,58 @@ def _special_interior(nx, ny, nz, dtype, seed):
     return inputs.to_dtype(a, dtype, px=px)
 
 
+def _rounding_grid(nx, ny, nz):
+    """FP64 grid whose interior exercises the exact-rounding paths of the residual
+    step, in z-slabs so that neighbours share a kind: values on a 2^-24 lattice
+    (their residuals hit binary32 rounding ties), tiny values (residuals in the
+    binary32 subnormal range), x*6 with 1 or 2 dropped bits and exact ties
+    (m = 2^52 + j and 1.5 * 2^52 + j, both signs, exponents -40..40), and large
+    values (residuals near and above the largest binary32)."""
+    rng = np.random.default_rng(11)
+    px = inputs.row_pitch(nx, "f64")
+    a = np.zeros((nz + 2, ny + 2, px), dtype=np.float64)
+    shape = (ny, nx)
+    for k in range(1, nz + 1):
+        kind = (k - 1) * 4 // nz
+        j = rng.integers(1, 4096, shape).astype(np.float64)
+        if kind == 0:
+            v = rng.integers(-8, 9, shape) + j * 2.0 ** -24
+        elif kind == 1:
+            v = (rng.random(shape) - 0.5) * 1e-39
+        elif kind == 2:
+            base = np.where(rng.random(shape) < 0.5, 1.0, 1.5)
+            sign = np.where(rng.random(shape) < 0.5, -1.0, 1.0)
+            e = rng.integers(-40, 41, shape).astype(np.float64)
+            v = sign * (base + j * 2.0 ** -52) * 2.0 ** e
+        else:
+            v = (rng.random(shape) - 0.5) * 1.2e38
+        a[k, 1:-1, 1:nx + 1] = v
+    return a
+
+
+@pytest.mark.parametrize("dtype", ["f32", "bf16"])
+def test_residual_rounding_edge_cases(dtype):
+    from paper_0912_4506_gb300 import api
+    nx, ny, nz = 61, 33, 24
+    u = _rounding_grid(nx, ny, nz)
+    px = inputs.row_pitch(nx, dtype)
+    e = inputs.to_dtype(np.zeros((nz + 2, ny + 2, px)), dtype, px=px)
+    e_same = np.zeros(u.shape, dtype=e.dtype)
+    w = min(u.shape[2], e.shape[2])
+    e_same[:, :, :w] = e[:, :, :w]
+    want_u, want_rho = oracle.residual_accumulate(u, e_same, nx=nx, dtype=dtype)
+    ug = api.as_grid(to_dev(u, "f64"), nx)
+    uo = api.alloc_like(ug)
+    uo.copy_(ug)
+    eg = api.as_grid(to_dev(e, dtype), nx)
+    rho = api.alloc_like(eg)
+    api.residual_accumulate(ug, uo, eg, rho)
+    got_u = to_host(uo, "f64")
+    got_rho = to_host(rho, dtype)
+    assert np.array_equal(got_u, want_u[:, :, :nx + 2])
+    assert np.array_equal(got_rho[1:-1, 1:-1, 1:-1], want_rho[1:-1, 1:-1, 1:nx + 1])
+
+
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
 @pytest.mark.parametrize("case", ["random", "special", "ragged"])
 def test_residual_accumulate_bit_exact(dtype, case):

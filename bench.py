@@ -65,7 +65,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--case", default="", help="profiling case: run only one kernel "
                    "configuration, e.g. --case sweep --dtype f32 --kernel tb --t 4 --size 384 "
-                   "(cases: sweep, rhs, residual, adjoint)")
+                   "(cases: sweep, rhs, residual, adjoint, batch: --size = number of grids)")
     p.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
     p.add_argument("--kernel", default="auto", choices=["auto", "plain", "tb"])
     p.add_argument("--size", type=int, default=NX)
@@ -613,6 +613,33 @@ def run_case(args):
                           "sweeps": args.sweeps, "ms": round(ms, 4),
                           "glups": round(n ** 3 * args.sweeps / ms / 1e6, 2)}), flush=True)
         j.close()
+        return
+    if args.case == "batch":
+        # the batched workload's first `n` grids (shapes and sweep counts from seed 2),
+        # depth 4 for every grid, one persistent launch without a CUDA graph
+        specs = inputs.batch_specs()[:n]
+        grids = []
+        for i, (gx, gy, gz, _) in enumerate(specs):
+            a = inputs.to_dtype(inputs.uniform_grid_f64(gx, gy, gz, g=i), "f32",
+                                px=inputs.row_pitch(gx, "f32"))
+            grids.append(api.from_numpy(a, gx, "cuda"))
+        b = api.Batch(grids, [sp[3] for sp in specs], t=[4] * len(specs), graph=False)
+        for _ in range(args.warmup):
+            b.run()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            b.run()
+        e1.record()
+        torch.cuda.synchronize()
+        b.check()
+        ms = e0.elapsed_time(e1) / args.steps
+        lups = sum(gx * gy * gz * sw for gx, gy, gz, sw in specs)
+        print(json.dumps({"case": "batch", "grids": len(specs), "ms": round(ms, 4),
+                          "glups": round(lups / ms / 1e6, 2)}), flush=True)
+        b.close()
         return
     if args.case == "residual":
         u0 = api.as_grid(inputs.laplace_boundary_torch(n, n, n, device="cuda"), n)

@@ -21,6 +21,9 @@ struct F64 {
     __device__ __forceinline__ static C ld(S v) { return v; }
     __device__ __forceinline__ static S st(C v) { return v; }
     __device__ __forceinline__ static C rnd(C v) { return v; }
+    // storage form of a value already representable in S
+    __device__ __forceinline__ static S st_exact(C v) { return v; }
+    __device__ __forceinline__ static void rnd_pair(C& a, C& b) {}
     __device__ __forceinline__ static C add(C a, C b) { return __dadd_rn(a, b); }
     __device__ __forceinline__ static C mul(C a, C b) { return __dmul_rn(a, b); }
     __device__ __forceinline__ static C sixth() { return 0x1.5555555555555p-3; }
@@ -33,6 +36,8 @@ struct F32 {
     __device__ __forceinline__ static C ld(S v) { return v; }
     __device__ __forceinline__ static S st(C v) { return v; }
     __device__ __forceinline__ static C rnd(C v) { return v; }
+    __device__ __forceinline__ static S st_exact(C v) { return v; }
+    __device__ __forceinline__ static void rnd_pair(C& a, C& b) {}
     __device__ __forceinline__ static C add(C a, C b) { return __fadd_rn(a, b); }
     __device__ __forceinline__ static C mul(C a, C b) { return __fmul_rn(a, b); }
     __device__ __forceinline__ static C sixth() { return 0x1.555556p-3f; }
@@ -51,6 +56,17 @@ struct BF16 {
         return __bfloat16_as_ushort(__float2bfloat16_rn(v));
     }
     __device__ __forceinline__ static C rnd(C v) { return ld(st(v)); }
+    // a float that is already a bf16 value: its high half
+    __device__ __forceinline__ static S st_exact(C v) {
+        return static_cast<S>(__float_as_uint(v) >> 16);
+    }
+    // round two floats to bf16 (nearest-even) with one packed conversion
+    __device__ __forceinline__ static void rnd_pair(C& a, C& b) {
+        const __nv_bfloat162 p = __floats2bfloat162_rn(a, b);
+        const uint32_t u = *reinterpret_cast<const uint32_t*>(&p);
+        a = __uint_as_float(u << 16);
+        b = __uint_as_float(u & 0xFFFF0000u);
+    }
     __device__ __forceinline__ static C add(C a, C b) { return __fadd_rn(a, b); }
     __device__ __forceinline__ static C mul(C a, C b) { return __fmul_rn(a, b); }
     __device__ __forceinline__ static C sixth() { return 0x1.555556p-3f; }

@@ -255,6 +255,7 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
             const C right = __shfl_down_sync(FULL, r[s - 1][CUR][0], 1);
             C out[V];
             if (zin) {
+                C val[V];
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
                     const C l = (e == 0) ? left : r[s - 1][CUR][e - 1];
@@ -265,9 +266,19 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
                     sum = Tr::add(sum, r[s - 1][OLD][e]);
                     sum = Tr::add(sum, r[s - 1][NEW][e]);
                     if (MODE == MODE_RHS) sum = Tr::add(sum, Tr::ld(vr.v[e]));
-                    const C val = Tr::rnd(Tr::mul(sum, c6));
-                    out[e] = (FAST || inxy[e]) ? val : r[s - 1][CUR][e];
+                    val[e] = Tr::mul(sum, c6);
                 }
+                // round to storage precision (bf16: two values per conversion; at
+                // depth 1 the one-value form measured faster)
+                if constexpr (V % 2 == 0 && T >= 2) {
+#pragma unroll
+                    for (int e = 0; e < V; e += 2) Tr::rnd_pair(val[e], val[e + 1]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e) val[e] = Tr::rnd(val[e]);
+                }
+#pragma unroll
+                for (int e = 0; e < V; ++e) out[e] = (FAST || inxy[e]) ? val[e] : r[s - 1][CUR][e];
             } else {
 #pragma unroll
                 for (int e = 0; e < V; ++e) out[e] = r[s - 1][CUR][e];
@@ -277,7 +288,7 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
                     r[s < T ? s : 0][NEW][e] = out[e];
-                    o.v[e] = Tr::st(out[e]);
+                    o.v[e] = Tr::st_exact(out[e]);  // already a storage value
                 }
                 *reinterpret_cast<Vec<S, V>*>(lvl + ((s - 1) * 2 + PAR) * PLANE + mycol) = o;
                 if (MODE == MODE_ADJ) adj_acc(out, q);
@@ -286,12 +297,14 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
                 if (all_out) {
                     Vec<S, V> ov;
 #pragma unroll
-                    for (int e = 0; e < V; ++e) ov.v[e] = Tr::st(out[e]);
+                    for (int e = 0; e < V; ++e)
+                        ov.v[e] = (T >= 2) ? Tr::st_exact(out[e]) : Tr::st(out[e]);
                     *reinterpret_cast<Vec<S, V>*>(dst + o) = ov;
                 } else {
 #pragma unroll
                     for (int e = 0; e < V; ++e)
-                        if (outxy[e]) dst[o + e] = Tr::st(out[e]);
+                        if (outxy[e])
+                            dst[o + e] = (T >= 2) ? Tr::st_exact(out[e]) : Tr::st(out[e]);
                 }
             }
         }

@@ -108,6 +108,9 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
     constexpr uint32_t kSlotBytes = (NSR > 0 ? 2 : 1) * kPlaneBytes;
     constexpr int OY = EY - 2 * T;
     static_assert(OY >= 1, "tile too small for the depth");
+    // level values are storage values already (every level is rounded): stores may
+    // take their bits without a conversion (used where it measured faster)
+    constexpr bool kExactStore = T >= 2 && MODE == MODE_PLAIN;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem);
     S* ring = reinterpret_cast<S*>(smem + L::HEADER);
     S* lvl = ring + NS * PLANE;
@@ -268,9 +271,11 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
                     if (MODE == MODE_RHS) sum = Tr::add(sum, Tr::ld(vr.v[e]));
                     val[e] = Tr::mul(sum, c6);
                 }
-                // round to storage precision (bf16: two values per conversion; at
-                // depth 1 the one-value form measured faster)
-                if constexpr (V % 2 == 0 && T >= 2) {
+                // round to storage precision (plain bf16 sweeps of depth >= 2: two
+                // values per conversion; the one-value form measured faster at depth
+                // 1 and, by two registers that cost a CTA per SM, for the bf16
+                // correction sweep at depth 2)
+                if constexpr (V % 2 == 0 && T >= 2 && MODE == MODE_PLAIN) {
 #pragma unroll
                     for (int e = 0; e < V; e += 2) Tr::rnd_pair(val[e], val[e + 1]);
                 } else {
@@ -288,7 +293,7 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
                     r[s < T ? s : 0][NEW][e] = out[e];
-                    o.v[e] = Tr::st_exact(out[e]);  // already a storage value
+                    o.v[e] = kExactStore ? Tr::st_exact(out[e]) : Tr::st(out[e]);
                 }
                 *reinterpret_cast<Vec<S, V>*>(lvl + ((s - 1) * 2 + PAR) * PLANE + mycol) = o;
                 if (MODE == MODE_ADJ) adj_acc(out, q);
@@ -298,13 +303,13 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
                     Vec<S, V> ov;
 #pragma unroll
                     for (int e = 0; e < V; ++e)
-                        ov.v[e] = (T >= 2) ? Tr::st_exact(out[e]) : Tr::st(out[e]);
+                        ov.v[e] = kExactStore ? Tr::st_exact(out[e]) : Tr::st(out[e]);
                     *reinterpret_cast<Vec<S, V>*>(dst + o) = ov;
                 } else {
 #pragma unroll
                     for (int e = 0; e < V; ++e)
                         if (outxy[e])
-                            dst[o + e] = (T >= 2) ? Tr::st_exact(out[e]) : Tr::st(out[e]);
+                            dst[o + e] = kExactStore ? Tr::st_exact(out[e]) : Tr::st(out[e]);
                 }
             }
         }

@@ -14,9 +14,12 @@ driver.
 Paper passages followed (Wittmann, Hager, Wellein, arXiv:0912.4506):
   * Eq. 1 (Sect. 1.1): one cell update, the mean of the six face neighbours.
   * Sect. 1.1: successive sweeps write grids A and B in turn.
-Readings where the paper is silent (multiply by RN(1/6), left-to-right sum in the
-order of Eq. 1, fixed boundary layer, bf16 rounding after every sweep, the
-residual/correction form of the refinement) are listed in the design doc.
+Readings where the paper is silent, as this module implements them: the sum is
+taken left to right in the order of Eq. 1 and multiplied by RN(1/6) of the
+compute precision (no division, no fused multiply-add); the boundary layer is
+fixed; bf16 values are rounded to nearest-even after every sweep; the refinement
+iterates corrections e' = (sum6(e) + rho) * RN(1/6) on a zero boundary with
+rho = sum6(u) - 6u computed in FP64.
 """
 import ctypes
 

@@ -64,25 +64,32 @@ __device__ __forceinline__ uint32_t mad_u(uint32_t a, uint32_t b, uint32_t c) {
 }
 
 __device__ __forceinline__ double add_pos_exact_f(double a, double b, uint32_t one) {
-    const uint32_t m1 = 0u - one, p20 = one << 20;  // hoisted out of the loops
+    const uint32_t m1 = 0u - one, p20 = one << 20, m20 = 0u - p20;  // hoisted out of the loops
     const unsigned long long A = (unsigned long long)__double_as_longlong(a);
     const unsigned long long B = (unsigned long long)__double_as_longlong(b);
     const bool swap = (uint32_t)(A >> 32) < (uint32_t)(B >> 32);
     const unsigned long long X = swap ? B : A;
     const unsigned long long Y = swap ? A : B;
-    const uint32_t ex = (uint32_t)(X >> 52);
-    const uint32_t d = mad_u((uint32_t)(Y >> 52), m1, ex);     // ex - ey
+    const uint32_t ex = (uint32_t)(X >> 52), ey = (uint32_t)(Y >> 52);
+    const uint32_t d = mad_u(ey, m1, ex);  // ex - ey
     const uint32_t dd = d > 31u ? 31u : d;
-    const unsigned long long kMant = 0x000FFFFFFFFFFFFFull, kHidden = 0x0010000000000000ull;
-    const unsigned long long mx = (X & kMant) | kHidden;
-    const unsigned long long my = (Y & kMant) | kHidden;
+    // significands with the hidden bit: the high word minus (exponent - 1) * 2^20,
+    // as multiply-adds (FMA pipe) instead of mask-and-or (integer ALU, the binding
+    // pipe of this sweep)
+    const unsigned long long mx =
+        ((unsigned long long)mad_u(ex, m20, mad_u(one, p20, (uint32_t)(X >> 32))) << 32) |
+        (uint32_t)X;
+    const unsigned long long my =
+        ((unsigned long long)mad_u(ey, m20, mad_u(one, p20, (uint32_t)(Y >> 32))) << 32) |
+        (uint32_t)Y;
     const uint32_t F = shl32((uint32_t)my, mad_u(dd, m1, 32u));  // 32 - dd
     const unsigned long long S = add64_f(mx, my >> dd, one);
     const uint32_t c = (uint32_t)(S >> 53);
     const unsigned long long Sn = S >> c;
     const uint32_t Fc = c ? (((uint32_t)S << 31) | (F >> 1) | (F & 1u)) : F;
-    const uint32_t up =
-        (uint32_t)(add64_f((unsigned long long)Fc, 0x7FFFFFFFull + (Sn & 1ull), one) >> 32);
+    const uint32_t up = (uint32_t)(add64_f((unsigned long long)Fc,
+                                           mad_u((uint32_t)Sn & 1u, one, 0x7FFFFFFFu), one) >>
+                                   32);
     const unsigned long long M = add64_f(Sn, (unsigned long long)up, one);
     // biased exponent (ex + c - 1) placed at bit 52 and added to M (no carry into
     // the low word: the shifted exponent has none)

@@ -42,16 +42,16 @@ ALGO_BYTES_PER_LUP = {"f64": 16, "f32": 8, "bf16": 4}
 TRAFFIC_PER_LAUNCH = {
     # profiles/plain_sweep_f64_emu6_384cubed.md: 487.9 MB read + 409.7 MB written
     # for 384^3 (56.6 M updates) -> x (512/384)^3
-    "plain_sweep_kernel<F64,emu=6>": round((487892736 + 409680896) * (512 / 384) ** 3),
+    "plain_sweep_kernel<F64,emu=6>": round((489529856 + 410431232) * (512 / 384) ** 3),
 }
 
 # Pipe cost of the FP64 plain sweep with 3 of its 5 additions on the integer
 # pipes (profiles/plain_sweep_f64_emu6_384cubed.md): FP64 pipe 3 ops per update at
-# 2 ops/clk/SM = 1.50 SM-cycles per update; the integer ALU pipe is busy 1.61
-# SM-cycles per update (ncu sm__pipe_alu_cycles_active 85.0 % of 706.9 k active
-# cycles per SMSP, 384^3 updates over 608 SMSPs, 4 SMSPs per SM).  The binding
-# pipe sets the ceiling: SMs x clock / max(1.50, 1.61).
-F64_EMU_SM_CYCLES_PER_LUP = {"fp64": 1.497, "alu": 1.613}
+# 2 ops/clk/SM = 1.50 SM-cycles per update (ncu 80.0 % of 697.2 k active cycles
+# per SMSP, 384^3 updates over 608 SMSPs, 4 SMSPs per SM); the integer ALU pipe is
+# busy 1.43 SM-cycles per update (76.4 %).  The binding pipe sets the ceiling:
+# SMs x clock / max(1.50, 1.43).
+F64_EMU_SM_CYCLES_PER_LUP = {"fp64": 1.498, "alu": 1.430}
 
 
 def parse():
@@ -528,9 +528,10 @@ def run_ours(args):
         if emu == 6:
             cyc = max(F64_EMU_SM_CYCLES_PER_LUP.values())
             peak_glups = SM_COUNT * mhz * 1e6 / cyc / 1e9
-            src = ("two-pipe ceiling: 152 SMs x %.0f MHz / max(FP64 pipe 1.50, integer ALU pipe "
-                   "1.61) SM-cycles per update (FP64 unit 2 ops/clk/SM; ALU cycles from ncu, "
-                   "profiles/plain_sweep_f64_emu6_384cubed.md)" % mhz)
+            src = ("two-pipe ceiling: 152 SMs x %.0f MHz / max(FP64 pipe %.2f, integer ALU "
+                   "pipe %.2f) SM-cycles per update (FP64 unit 2 ops/clk/SM; ALU cycles from "
+                   "ncu, profiles/plain_sweep_f64_emu6_384cubed.md)"
+                   % (mhz, F64_EMU_SM_CYCLES_PER_LUP["fp64"], F64_EMU_SM_CYCLES_PER_LUP["alu"]))
         else:
             peak_glups = fp64_only
             src = ("FP64 pipe: %d DP ops/clk/SM x %d SMs x %.0f MHz / 6 ops per update"

@@ -175,7 +175,10 @@ class HostPipeline:
     Problem i is uploaded, swept and downloaded through handle i % 2; each handle
     owns a device grid pair and launches on its own stream, so one problem's
     host<->device copies overlap the other problem's sweeps (the host link, about
-    200 GB/s each way on GB300, is otherwise idle while the sweeps run)."""
+    200 GB/s each way on GB300, is otherwise idle while the sweeps run).  The
+    sweeps themselves run one problem after the other (an event orders problem
+    i's sweeps after problem i-1's): two problems sweeping at once only share the
+    SMs."""
 
     def __init__(self, nx, ny, nz, dtype="f64", device="cuda"):
         self.device = torch.device(device)
@@ -194,8 +197,16 @@ class HostPipeline:
             cur = torch.cuda.current_stream(self.device)
             for st in self.streams:
                 st.wait_stream(cur)
+            prev = None
             for i, (hi, ho) in enumerate(zip(host_ins, host_outs)):
-                self.jobs[i % 2].run_host(hi, ho, nsweeps, t, kernel)
+                j, st = self.jobs[i % 2], self.streams[i % 2]
+                j.upload(hi)
+                if prev is not None:
+                    st.wait_event(prev)
+                fb = _lib.jacobi_sweep_ex(j._h, nsweeps, t, kernel)
+                prev = torch.cuda.Event()
+                prev.record(st)
+                j.download(ho, fb)
             for st in self.streams:
                 cur.wait_stream(st)
 

@@ -564,7 +564,10 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (1.09 GB per grid), no flush"},
         "roofline": roof,
-        "gpu_launches": launches_per_step * args.steps,
+        # the sweep passes plus, for the FP64 sweep with integer-pipe additions,
+        # the range check launched once per sweep call
+        "gpu_launches": (launches_per_step + (1 if plan.get("emu_adds", 0) > 0 else 0))
+                        * args.steps,
         "e2e": {"value": round(e2e_value, 3), "unit": "GLUP/s",
                 "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
                 "overlap": "2 handles on 2 streams: a step's copies overlap the next "

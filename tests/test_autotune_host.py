@@ -1,0 +1,37 @@
+"""Host logic of the depth autotuner, without a GPU: the measurement is replaced
+by a fake whose best depth is known; the first call measures every candidate of
+every new shape and caches the result, the second reads the cache only."""
+import json
+import types
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+
+def test_tune_measures_once_then_uses_cache(tmp_path, monkeypatch):
+    from paper_0912_4506_gb300 import autotune
+    monkeypatch.setenv("JACOBI_GB300_CACHE", str(tmp_path))
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda dev=None: "FakeGPU")
+    monkeypatch.setattr(torch.cuda, "get_device_properties",
+                        lambda dev=None: types.SimpleNamespace(multi_processor_count=152))
+    calls = []
+
+    def fake_time(shape, dtype, t, sweeps, device, reps):
+        calls.append((shape, t))
+        best = 4 if shape[0] >= 100 else 2  # rate peaks at the shape's best depth
+        return 1e9 * (10.0 - abs(t - best))
+
+    monkeypatch.setattr(autotune, "_time_shape", fake_time)
+    shapes = [(128, 64, 64), (40, 40, 40), (128, 64, 64)]
+    ts, table = autotune.tune(shapes, "f32", candidates=(2, 3, 4, 5), device="cpu")
+    assert ts == [4, 2, 4]
+    # two distinct shapes x four candidates (the repeated shape is measured once)
+    assert len(calls) == 8
+    cached = json.loads((tmp_path / "autotune.json").read_text())
+    assert cached["FakeGPU|f32|128x64x64"]["t"] == 4
+    assert cached["FakeGPU|f32|40x40x40"]["t"] == 2
+
+    calls.clear()
+    ts2, _ = autotune.tune(shapes, "f32", candidates=(2, 3, 4, 5), device="cpu")
+    assert ts2 == ts and calls == []

@@ -128,7 +128,9 @@ JAC_API int jacobi_plan(jacobi_t h, int nsweeps, int t, int kernel, jacobi_plan_
  *   e' = (((((( e[i-1] + e[i+1]) + e[j-1]) + e[j+1]) + e[k-1]) + e[k+1]) + rho) * RN(1/6)
  * on the handle's grids (A = e on entry, boundary layer zero), the Jacobi
  * iteration of (I - J0) e = rho/6 with J0 the sweep of Eq. 1 on a zero
- * boundary.  rho: device grid of the handle's dtype and layout (read only).
+ * boundary.  rho: device grid of the handle's dtype and layout (read only, not
+ * written while the call's kernels run; 16-byte aligned, else JAC_EINVAL: it is
+ * read through a TMA descriptor, which the handle caches for the last rho seen).
  * dtype JAC_F32 or JAC_BF16 (JAC_EUNSUPPORTED otherwise).  t, final_is_b as in
  * jacobi_sweep (t = 0: depth 4 for FP32, 2 for bf16).
  */

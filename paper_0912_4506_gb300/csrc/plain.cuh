@@ -200,13 +200,15 @@ __global__ void __launch_bounds__(32 * WY)
     const int k1 = min(g.nz, k0 + kchunk - 1);
 
     // the lane's vector lies inside the row allocation (needed for shuffles even
-    // when none of its cells is interior)
+    // when none of its cells is interior); the FP64 march loads cell by cell, so
+    // there a vector that runs past the row still updates its interior cells
     const bool loadable = (x0 + V) <= g.px;
+    constexpr bool kPerCellLoads = sizeof(typename Tr::S) == 8;
     bool interior[V];
     bool all_interior = true;
 #pragma unroll
     for (int e = 0; e < V; ++e) {
-        interior[e] = loadable && (x0 + e >= 1) && (x0 + e <= g.nx);
+        interior[e] = (kPerCellLoads || loadable) && (x0 + e >= 1) && (x0 + e <= g.nx);
         all_interior = all_interior && interior[e];
     }
     const bool left_ok = (x0 >= 1);

@@ -59,3 +59,10 @@ def test_create_rejects_bad_arguments_without_device(lib):
         assert rc == _lib.JAC_EINVAL, (nx, ny, nz, dt, pitch, rc)
     assert lib.jacobi_sweep(None, 1, 0, None) == _lib.JAC_EINVAL
     assert lib.jacobi_destroy(None) == _lib.JAC_OK
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No CPU fallback: a missing shared library raises at load time."""
+    from paper_0912_4506_gb300 import _lib
+    with pytest.raises(RuntimeError, match="CUDA library missing"):
+        _lib.load(str(tmp_path / "libjacobi_gb300.so"))

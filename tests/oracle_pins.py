@@ -195,6 +195,58 @@ def pin_rhs_sweep(lib):
         assert np.all(got[1:-1, 1:-1, 1:-1] == 1.0) and got[0].sum() == 0
 
 
+def pin_rhs_sweep_bf16(lib):
+    """bf16 correction sweep, values derived by hand (c32 = RN32(1/6) =
+    0x1.555556p-3, so 6*c32 = 1 + 2^-25 exactly):
+      * e = 0, rho = 6: (0 + 6) * c32 = 1 + 2^-25 -> RN32 1 -> bf16 1.0 (0x3F80);
+      * e = 6 at the i-1 neighbour of the centre of a 3^3 interior (zero
+        elsewhere), rho = 18 * 2^-8 (bf16-exact): the sum is 6 + 18 * 2^-8 exactly,
+        times c32 is (1 + 3 * 2^-8)(1 + 2^-25) -> RN32 1 + 3 * 2^-8, which lies
+        half-way between the bf16 values 1 + 2^-7 (0x3F81, odd) and 1 + 2^-6
+        (0x3F82, even): nearest-even gives 0x3F82.  Without rho the centre would
+        be RN(6 * c32) = 1.0 (0x3F80); truncation would give 0x3F81.
+    """
+    z = np.zeros((5, 5, 5), dtype=np.uint16)
+    six = np.full_like(z, 0x40C0)  # 6.0
+    got = oracle.rhs_sweeps(z, six, 1, dtype="bf16", lib=lib)
+    assert np.all(got[1:-1, 1:-1, 1:-1] == 0x3F80), got[2, 2, 2]
+    assert np.all(got[0] == 0) and np.all(got[:, :, 0] == 0)
+    e = np.zeros((5, 5, 5), dtype=np.uint16)
+    e[2, 2, 1] = 0x40C0          # 6.0 at (i, j, k) = (1, 2, 2)
+    rho = np.zeros_like(e)
+    rho[2, 2, 2] = 0x3D90        # 18 * 2^-8 = 1.125 * 2^-4 at the centre
+    assert float(oracle.bf16_to_f32(rho[2, 2, 2:3], lib=lib)[0]) == 18 * 2.0 ** -8
+    got = oracle.rhs_sweeps(e, rho, 1, dtype="bf16", lib=lib)
+    assert int(got[2, 2, 2]) == 0x3F82, hex(int(got[2, 2, 2]))
+    # the cell at (2, 2, 2)'s i+1 side sees only its own zero neighbours and rho 0
+    assert int(got[2, 2, 3]) == 0
+
+
+def pin_residual_bf16_store(lib):
+    """The bf16 residual store: rho = s(u) - 6u is exactly 2a on u = a * x^2
+    (x the padded i index), so choosing a puts the residual on or next to a bf16
+    rounding tie (the value is exact in FP64 and FP32, so only the bf16 rounding
+    acts):  2a = 1 + 2^-8 is the tie between 0x3F80 and 0x3F81 -> 0x3F80 (even);
+    2a = 1 + 3 * 2^-8 ties between 0x3F81 and 0x3F82 -> 0x3F82 (even);
+    2a = 1 + 2^-8 + 2^-20 lies just above a tie -> 0x3F81.  A bf16 correction e
+    is widened exactly and added on the interior only."""
+    nx, ny, nz = 5, 4, 3
+    k, j, i = np.meshgrid(np.arange(nz + 2), np.arange(ny + 2), np.arange(nx + 2),
+                          indexing="ij")
+    interior = ((i >= 1) & (i <= nx) & (j >= 1) & (j <= ny) & (k >= 1) & (k <= nz))
+    for two_a, want in ((1 + 2.0 ** -8, 0x3F80), (1 + 3 * 2.0 ** -8, 0x3F82),
+                        (1 + 2.0 ** -8 + 2.0 ** -20, 0x3F81)):
+        u = (two_a / 2) * (i * i).astype(np.float64)
+        e = np.zeros(u.shape, dtype=np.uint16)
+        u1, rho = oracle.residual_accumulate(u, e, dtype="bf16", lib=lib)
+        assert np.all(rho[interior] == want), (two_a, np.unique(rho[interior]))
+        assert np.all(rho[~interior] == 0)
+    q = (i * i).astype(np.float64)
+    e = np.where(interior, 0x3E80, 0x4000).astype(np.uint16)  # 0.25 inside, 2.0 outside
+    u1, _ = oracle.residual_accumulate(q, e, dtype="bf16", lib=lib)
+    assert np.array_equal(u1, np.where(interior, q + 0.25, q))
+
+
 def pin_refinement_equals_plain(lib):
     """In exact arithmetic u + sum_{k<m} J0^k (J u - u) = J^m u, so O outer steps of
     m inner correction sweeps equal O*m plain sweeps (FP64: rounding only)."""
@@ -254,5 +306,6 @@ def pin_gradient_structure(lib):
 
 ALL_PINS = [pin_hand_4cubed, pin_sum_order, pin_harmonic_fixed_points, pin_sine_modes,
             pin_bf16_conversion, pin_bf16_sweep_is_rounded_f32, pin_residual,
-            pin_rhs_sweep, pin_refinement_equals_plain, pin_gradient_fd,
+            pin_rhs_sweep, pin_rhs_sweep_bf16, pin_residual_bf16_store,
+            pin_refinement_equals_plain, pin_gradient_fd,
             pin_gradient_structure]

@@ -1,7 +1,8 @@
 """Plant plausible mistakes in copies of the oracle (on the CPU) and check that
 the pins catch every one: a dropped term, a wrong index, a wrong sign, a divide
 instead of the rounded 1/6 product, a reordered sum, a
-truncating bf16 conversion, a lost boundary gradient, a wrong residual.
+truncating bf16 conversion, a lost boundary gradient, a wrong residual, a
+correction sweep that drops rho, a truncating or unconverted bf16 residual path.
 """
 import os
 
@@ -62,6 +63,13 @@ MUTATIONS = {
                            "                    double lam_sum = lam[LIN(i, j, k)];"),
     "residual_sign": ("                double r = s - six_u;", "                double r = six_u - s;"),
     "residual_no_accumulate": ("                u[x] = u[x] + ev;", "                (void)ev;"),
+    "rhs_drops_rho_bf16": ("                    v = v + bf16_to_f32(rho[LIN(i, j, k)]);\n",
+                           ""),
+    "residual_bf16_truncate": ("                else                ((uint16_t *)rho)[x] = f32_to_bf16((float)r);",
+                               "                else { float fr = (float)r; uint32_t ub; memcpy(&ub, &fr, 4);\n"
+                               "                       ((uint16_t *)rho)[x] = (uint16_t)(ub >> 16); }"),
+    "residual_bf16_widen_wrong": ("                else                ev = (double)bf16_to_f32(((const uint16_t *)e)[x]);",
+                                  "                else                ev = (double)((const uint16_t *)e)[x];"),
     "rhs_drops_rho_f32": ("                    v = v + rho[LIN(i, j, k)];\n                    b[LIN(i, j, k)] = v * c;",
                           "                    b[LIN(i, j, k)] = v * c;"),
 }

@@ -30,28 +30,21 @@ sys.path.insert(0, ROOT)
 
 NX = NY = NZ = 512
 NSWEEPS = 100
-DP_OPS_PER_LUP = 6          # 5 adds + 1 multiply (Eq. 1)
-SM_COUNT = 152
-DP_OPS_PER_CLK_PER_SM = 2   # GB300 FP64: 1.25 TFLOP/s nominal with FMA counted as 2
 ALGO_BYTES_PER_LUP = {"f64": 16, "f32": 8, "bf16": 4}
 
-# DRAM bytes per launch of the dominant kernel from the ncu captures committed
-# under profiles/ (None when no capture of the current kernel exists).  The 512^3
-# figure scales the 384^3 capture by the lattice-site updates (traffic is
-# proportional to them: 16 B per update, no re-reads).
+# DRAM bytes per launch of the dominant kernel, from an ncu capture of the same
+# kernel on a 384^3 grid (dram__bytes_read.sum + dram__bytes_write.sum), scaled
+# to 512^3 by the lattice-site updates (traffic is proportional to them: 16 B per
+# update, no re-reads).  A kernel without a capture of its current code: None.
 TRAFFIC_PER_LAUNCH = {
-    # profiles/plain_sweep_f64_emu6_384cubed.md: 487.9 MB read + 409.7 MB written
-    # for 384^3 (56.6 M updates) -> x (512/384)^3
     "plain_sweep_kernel<F64,emu=6>": round((489529856 + 410431232) * (512 / 384) ** 3),
 }
 
-# Pipe cost of the FP64 plain sweep with 3 of its 5 additions on the integer
-# pipes (profiles/plain_sweep_f64_emu6_384cubed.md): FP64 pipe 3 ops per update at
-# 2 ops/clk/SM = 1.50 SM-cycles per update (ncu 80.0 % of 697.2 k active cycles
-# per SMSP, 384^3 updates over 608 SMSPs, 4 SMSPs per SM); the integer ALU pipe is
-# busy 1.43 SM-cycles per update (76.4 %).  The binding pipe sets the ceiling:
-# SMs x clock / max(1.50, 1.43).
-F64_EMU_SM_CYCLES_PER_LUP = {"fp64": 1.498, "alu": 1.430}
+# Pipe-rate probes (jacobi_pipe_probe): launch shape and operations per update of
+# the FP64 sweep with 3 of its 5 additions on the integer pipes.
+PROBE_BLOCKS_PER_SM, PROBE_THREADS = 8, 256
+F64_UNIT_OPS_PER_LUP = {"all_fp64": 6, "emu3": 3}   # FP64-unit operations per update
+EMU_ADDS_PER_LUP = 3
 
 
 def parse():
@@ -65,7 +58,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--case", default="", help="profiling case: run only one kernel "
                    "configuration, e.g. --case sweep --dtype f32 --kernel tb --t 4 --size 384 "
-                   "(cases: sweep, rhs, residual, adjoint, batch: --size = number of grids)")
+                   "(cases: sweep, rhs, residual, adjoint, batch: --size = number of grids, "
+                   "peaks: the pipe-rate probes)")
     p.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
     p.add_argument("--kernel", default="auto", choices=["auto", "plain", "tb"])
     p.add_argument("--size", type=int, default=NX)
@@ -165,51 +159,90 @@ def make_input(dtype="f64"):
     return a if dtype == "f64" else inputs.to_dtype(a, dtype)
 
 
-def cpu_oracle_rate(a64, budget_s=12.0, max_sweeps=100):
-    """Time the CPU oracle (as it stands, OpenMP over k on every host core) on
-    the 512^3 FP64 grid; returns (GLUP/s, cores, sample description)."""
+def cpu_oracle_rate(a64, nsweeps=NSWEEPS):
+    """Time the CPU oracle as it stands (OpenMP over k on every host core) on the
+    512^3 FP64 grid: one call of `nsweeps` sweeps on two preallocated grids (no
+    copies inside the timed call).  Returns (GLUP/s, cores, sample description)."""
     import oracle
     cores = os.cpu_count() or 1
+    A = a64.copy()
+    B = a64.copy()
     t0 = time.perf_counter()
-    oracle.sweeps(a64, 1, nx=NX, nthreads=cores)
-    one = time.perf_counter() - t0
-    n = int(max(1, min(max_sweeps, budget_s / max(one, 1e-6))))
-    t0 = time.perf_counter()
-    oracle.sweeps(a64, n, nx=NX, nthreads=cores)
+    oracle.sweeps_into(A, B, nsweeps, nx=NX, nthreads=cores)
     dt = time.perf_counter() - t0
-    rate = NX * NY * NZ * n / dt / 1e9
-    return rate, cores, f"{n} sweeps of the 512^3 FP64 grid (same seeds), {dt:.1f} s"
+    rate = NX * NY * NZ * nsweeps / dt / 1e9
+    return rate, cores, f"{nsweeps} sweeps of the 512^3 FP64 grid (same seeds), {dt:.1f} s"
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, on the same workload (every
+    step = the 100 sweeps of the 512^3 FP64 grid, one oracle call on two
+    preallocated grids).  Under torchrun only rank 0 runs it."""
     world, rank, _ = dist_setup()
     if rank != 0:
         return
     import oracle
     a64 = make_input("f64")
     cores = os.cpu_count() or 1
-    per_step = 8
+    A = a64.copy()
+    B = a64.copy()
     for _ in range(args.warmup):
-        oracle.sweeps(a64, per_step, nx=NX, nthreads=cores)
+        oracle.sweeps_into(A, B, NSWEEPS, nx=NX, nthreads=cores)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        oracle.sweeps(a64, per_step, nx=NX, nthreads=cores)
+        oracle.sweeps_into(A, B, NSWEEPS, nx=NX, nthreads=cores)
     dt = time.perf_counter() - t0
-    value = NX * NY * NZ * per_step * args.steps / dt / 1e9
+    value = NX * NY * NZ * NSWEEPS * args.steps / dt / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value,
         "unit": "GLUP/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "nz": NZ,
-                   "sweeps_per_step": per_step, "l2": "inputs larger than L2",
-                   "sample": f"bounded: {per_step} of the workload's 100 sweeps per step"},
+                   "sweeps_per_step": NSWEEPS, "l2": "inputs larger than L2"},
         "cpu_baseline": {"value": value, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{per_step} sweeps of the 512^3 FP64 grid per step"},
+                         "sample": f"{NSWEEPS} sweeps of the 512^3 FP64 grid per step, "
+                                   f"{args.steps} steps"},
         "e2e": {"value": value, "unit": "GLUP/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def measure_pipes(dev):
+    """Operations per second of each pipe-rate probe on this GPU (CUDA events,
+    after a warm-up launch), in Gop/s."""
+    import torch
+    from paper_0912_4506_gb300 import _lib
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = sms * PROBE_BLOCKS_PER_SM
+    out = torch.empty(blocks * PROBE_THREADS, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    res = {}
+    kinds = {"dadd": _lib.JAC_PROBE_DADD, "fadd": _lib.JAC_PROBE_FADD,
+             "lop3": _lib.JAC_PROBE_LOP3, "imad": _lib.JAC_PROBE_IMAD,
+             "emu_add": _lib.JAC_PROBE_EMU_ADD}
+    iters = {"dadd": 2048, "fadd": 16384, "lop3": 8192, "imad": 8192, "emu_add": 1024}
+    for name, kind in kinds.items():
+        it = iters[name]
+        _lib.jacobi_pipe_probe(kind, out.data_ptr(), blocks, PROBE_THREADS, it,
+                               stream.cuda_stream)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            _lib.jacobi_pipe_probe(kind, out.data_ptr(), blocks, PROBE_THREADS, it,
+                                   stream.cuda_stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        ops = blocks * PROBE_THREADS * it * _lib.JAC_PROBE_CHAINS
+        res[name + "_gops"] = round(ops / ms / 1e6, 2)
+    res["launch"] = {"blocks": blocks, "threads": PROBE_THREADS,
+                     "chains_per_thread": _lib.JAC_PROBE_CHAINS}
+    return res
 
 
 # ---------------------------------------------------------------------------
@@ -229,23 +262,39 @@ def time_sweeps(j, nsweeps, t, kernel, steps, warmup, stream):
 
 
 def variant_rows(dev, steps):
-    """GLUP/s of the other paths on the same GPU (beside the plain FP64 form)."""
+    """GLUP/s of every kernel family and depth on the same GPU, beside the plain
+    form (keys name the depth actually run; a depth with no kernel is recorded as
+    not built, from the library's own rejection).  FP64 rows also state the
+    multiple of the plain FP64 sweep."""
     import torch
-    from paper_0912_4506_gb300 import api
+    from paper_0912_4506_gb300 import _lib, api
     rows = {}
     stream = torch.cuda.current_stream()
     for dtype in ("f64", "f32", "bf16"):
         j = api.Jacobi(api.from_numpy(make_input(dtype), NX, dev))
-        tmax = 4 if dtype == "f64" else 8
-        for t, kern, name in [(1, api.JAC_KERNEL_PLAIN, "plain")] + \
-                [(t, api.JAC_KERNEL_TB, f"tb_t{t}") for t in (1, 2, 3, 4, 8, 16)
-                 if t <= tmax or dtype == "f64"]:
+        code = {"f64": _lib.JAC_F64, "f32": _lib.JAC_F32, "bf16": _lib.JAC_BF16}[dtype]
+        tmax = _lib.jacobi_max_depth(code, _lib.JAC_OP_SWEEP)
+        cases = [(1, api.JAC_KERNEL_PLAIN, "plain")] + \
+            [(t, api.JAC_KERNEL_TB, f"tb_t{t}") for t in range(1, tmax + 1)] + \
+            [(16, api.JAC_KERNEL_TB, "tb_t16")]
+        plain_glups = None
+        for t, kern, name in cases:
+            try:
+                plan = j.plan(NSWEEPS, t, kern)
+            except _lib.JacobiError as e:
+                rows[f"{dtype}_{name}"] = {"not_built": str(e)}
+                continue
+            assert plan["t"] == t, (dtype, t, plan["t"])
             ms = time_sweeps(j, NSWEEPS, t, kern, steps, 1, stream)
-            plan = j.plan(NSWEEPS, t, kern)
-            rows[f"{dtype}_{name}"] = {
-                "glups": round(NX * NY * NZ * NSWEEPS / ms / 1e6, 2),
-                "ms_per_100_sweeps": round(ms, 3), "t_used": plan["t"],
-                "remainder_t": plan["remainder_t"]}
+            glups = NX * NY * NZ * NSWEEPS / ms / 1e6
+            row = {"glups": round(glups, 2), "ms_per_100_sweeps": round(ms, 3),
+                   "t_used": plan["t"], "remainder_t": plan["remainder_t"],
+                   "tile": [plan["ext_x"], plan["ext_y"]], "emu_adds": plan["emu_adds"]}
+            if name == "plain":
+                plain_glups = glups
+            elif dtype == "f64" and plain_glups:
+                row["multiple_of_plain"] = round(glups / plain_glups, 3)
+            rows[f"{dtype}_{name}"] = row
         j.close()
         del j
         torch.cuda.empty_cache()
@@ -519,40 +568,31 @@ def run_ours(args):
     kname = (f"plain_sweep_kernel<F64,emu={emu}>" if plan["kernel"] == 1
              else f"tb_sweep_kernel<F64,T={plan['t']}>")
     launch_s = ms_step / 1e3 / launches_per_step
-    sweeps_per_launch = NSWEEPS / launches_per_step
-    if plan["kernel"] == 1:
-        mhz = pk.get("sm_max_mhz", 2070.0)
-        lups_launch = NX * NY * NZ * sweeps_per_launch
-        achieved_glups = lups_launch / launch_s / 1e9
-        fp64_only = DP_OPS_PER_CLK_PER_SM * SM_COUNT * mhz * 1e6 / DP_OPS_PER_LUP / 1e9
-        if emu == 6:
-            cyc = max(F64_EMU_SM_CYCLES_PER_LUP.values())
-            peak_glups = SM_COUNT * mhz * 1e6 / cyc / 1e9
-            src = ("two-pipe ceiling: 152 SMs x %.0f MHz / max(FP64 pipe %.2f, integer ALU "
-                   "pipe %.2f) SM-cycles per update (FP64 unit 2 ops/clk/SM; ALU cycles from "
-                   "ncu, profiles/plain_sweep_f64_emu6_384cubed.md)"
-                   % (mhz, F64_EMU_SM_CYCLES_PER_LUP["fp64"], F64_EMU_SM_CYCLES_PER_LUP["alu"]))
-        else:
-            peak_glups = fp64_only
-            src = ("FP64 pipe: %d DP ops/clk/SM x %d SMs x %.0f MHz / 6 ops per update"
-                   % (DP_OPS_PER_CLK_PER_SM, SM_COUNT, mhz))
-        roof = {"bound": "alu", "achieved": round(achieved_glups, 3),
-                "peak": round(peak_glups, 3), "unit": "GLUP/s",
-                "frac": round(achieved_glups / peak_glups, 4),
-                "traffic": TRAFFIC_PER_LAUNCH.get(kname), "kernel": kname,
-                "peak_source": src,
-                "fp64_unit_only_peak": round(fp64_only, 3),
-                "frac_vs_fp64_unit_only": round(achieved_glups / fp64_only, 4),
-                "hbm_frac": round(ALGO_BYTES_PER_LUP["f64"] * lups_launch / launch_s / 1e9
-                                  / pk["hbm_gbs"], 4)}
-    else:
-        bytes_launch = ALGO_BYTES_PER_LUP["f64"] * NX * NY * NZ
-        achieved = bytes_launch / launch_s / 1e9
-        roof = {"bound": "hbm", "achieved": round(achieved, 1), "peak": pk["hbm_gbs"],
-                "unit": "GB/s", "frac": round(achieved / pk["hbm_gbs"], 4),
-                "traffic": TRAFFIC_PER_LAUNCH.get(kname), "kernel": kname,
-                "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({pk_src})"}
-    roof["launch_ms"] = round(launch_s * 1e3, 4)
+    lups_launch = NX * NY * NZ * NSWEEPS / launches_per_step
+    bytes_launch = ALGO_BYTES_PER_LUP["f64"] * NX * NY * NZ
+    achieved_gbs = bytes_launch / launch_s / 1e9
+    achieved_glups = lups_launch / launch_s / 1e9
+    # arithmetic ceilings from the pipe-rate probes measured in this run: the FP64
+    # unit doing all 6 operations of an update, and this kernel's mix (FP64-unit
+    # operations and integer-pipe additions, each at its measured rate, the two
+    # pipes taken as independent)
+    pipes = measure_pipes(dev)
+    fp64_only = pipes["dadd_gops"] / F64_UNIT_OPS_PER_LUP["all_fp64"]
+    pipes["fp64_unit_only_ceiling_glups"] = round(fp64_only, 2)
+    pipes["frac_vs_fp64_unit_only"] = round(achieved_glups / fp64_only, 4)
+    if emu > 0 and plan["kernel"] == 1 and emu == 6:
+        mix = min(pipes["dadd_gops"] / F64_UNIT_OPS_PER_LUP["emu3"],
+                  pipes["emu_add_gops"] / EMU_ADDS_PER_LUP)
+        pipes["kernel_mix_ceiling_glups"] = round(mix, 2)
+        pipes["frac_vs_kernel_mix"] = round(achieved_glups / mix, 4)
+    pipes["hbm_ceiling_glups"] = round(pk["hbm_gbs"] / ALGO_BYTES_PER_LUP["f64"], 2)
+    roof = {"bound": "hbm", "achieved": round(achieved_gbs, 1), "peak": pk["hbm_gbs"],
+            "unit": "GB/s", "frac": round(achieved_gbs / pk["hbm_gbs"], 4),
+            "traffic": TRAFFIC_PER_LAUNCH.get(kname), "kernel": kname,
+            "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({pk_src})",
+            "algorithmic_bytes_per_launch": bytes_launch,
+            "launch_ms": round(launch_s * 1e3, 4), "achieved_glups": round(achieved_glups, 3),
+            "pipes": pipes}
 
     line = {
         "metric": METRIC,
@@ -598,6 +638,10 @@ def run_case(args):
     import torch
     from paper_0912_4506_gb300 import api, inputs
     n = args.size
+    if args.case == "peaks":
+        print(json.dumps({"case": "peaks", **measure_pipes(torch.device("cuda", 0))}),
+              flush=True)
+        return
     if args.case == "adjoint":
         px = inputs.row_pitch(n, args.dtype)
         W = api.from_numpy(inputs.to_dtype(inputs.normal_grid_f64(n, n, n), args.dtype, px=px),

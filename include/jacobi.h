@@ -61,6 +61,13 @@ enum jac_status {
 
 typedef enum { JAC_F64 = 0, JAC_F32 = 1, JAC_BF16 = 2 } jac_dtype;
 
+/* Operations, for jacobi_max_depth(). */
+typedef enum {
+    JAC_OP_SWEEP = 0,      /* jacobi_sweep / jacobi_sweep_ex (Eq. 1)               */
+    JAC_OP_RHS = 1,        /* jacobi_sweep_rhs (correction sweeps)                 */
+    JAC_OP_ADJOINT = 2     /* jacobi_adjoint (transpose sweeps)                    */
+} jac_op;
+
 /* Kernel selection for jacobi_sweep_ex(). */
 typedef enum {
     JAC_KERNEL_AUTO = 0,   /* planner: plain streaming or temporal blocking        */
@@ -102,11 +109,15 @@ JAC_API int jacobi_create(jacobi_t *out, int nx, int ny, int nz, int dtype, void
 
 /*
  * jacobi_sweep — nsweeps sweeps of Eq. 1, A -> B -> A ... (Sect. 1.1).
- *   t          temporal-blocking depth request: 0 = planner's choice (FP64: 1,
- *              FP32/bf16: 3), 1 = one sweep per pass (FP64: the register-march
- *              streaming kernel; FP32/bf16: the TMA-ring kernel at depth 1),
- *              t >= 2 = passes of depth min(t, deepest feasible) with a shallower
- *              last pass when t does not divide nsweeps.
+ *   t          temporal-blocking depth request (Sect. 1.3): 0 = planner's choice
+ *              (FP64: 1, FP32/bf16: 3), 1 = one sweep per pass (FP64: the
+ *              register-march streaming kernel; FP32/bf16: the TMA-ring kernel at
+ *              depth 1), t >= 2 = passes of depth min(t, nsweeps) with a shallower
+ *              last pass when t does not divide nsweeps.  A depth deeper than the
+ *              deepest kernel built (jacobi_max_depth: 8 for every dtype) is
+ *              rejected with JAC_EUNSUPPORTED before anything is launched: an
+ *              extended tile of depth t needs more than 2t rows, and one warp per
+ *              row caps a CTA at 32 rows, so depth 16 has no kernel.
  *   final_is_b set to 1 when the result is in B, else 0.  Every pass (one plain
  *              sweep, or one blocked pass of several sweeps) reads one grid and
  *              writes the other, so this is the parity of the number of passes.
@@ -120,7 +131,7 @@ JAC_API int jacobi_sweep(jacobi_t h, int nsweeps, int t, int *final_is_b);
 JAC_API int jacobi_sweep_ex(jacobi_t h, int nsweeps, int t, int kernel, int *final_is_b);
 
 /* jacobi_plan — fill *info with the plan jacobi_sweep_ex(h, nsweeps, t, kernel)
- * would execute, without launching anything. */
+ * would execute, without launching anything (same return codes). */
 JAC_API int jacobi_plan(jacobi_t h, int nsweeps, int t, int kernel, jacobi_plan_info *info);
 
 /*
@@ -234,29 +245,35 @@ JAC_API int jacobi_batch_destroy(jacobi_batch_t b);
 /*
  * jacobi_sweep_noalloc — jacobi_sweep for callers that cannot allocate device
  * memory: code running where cudaMalloc is not allowed or not wanted, such as a
- * host framework that owns every device byte through its own pool, a plug-in
- * that must not grow the process's device footprint, or code being recorded
- * into a CUDA graph.  There is no counterpart in the paper; it is a deployment
- * convenience.  No handle is needed and nothing is allocated: the second
- * (ping-pong) grid and the device status word live in one static device array
- * of JAC_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU that
- * loads the library keeps until the process exits.
+ * host framework that owns every device byte through its own pool allocator, or
+ * a plug-in that must not grow the process's device footprint while it runs.
+ * There is no counterpart in the paper; it is a deployment convenience.  No
+ * handle is needed and the call allocates nothing: the second (ping-pong) grid,
+ * the device status word and the FP64 range flag live in one static device
+ * array of JAC_NOALLOC_SCRATCH_BYTES bytes inside the library, which every GPU
+ * that loads the library keeps until the process exits.
  *   grid       the caller's device grid (layout as above): input on entry,
  *              result on return (the library copies the result back when the
  *              last pass ends in the scratch grid).  Row padding is not touched.
- *   nsweeps, t as in jacobi_sweep.
+ *   nsweeps, t as in jacobi_sweep; the call runs the kernels jacobi_sweep runs
+ *              with the same arguments (same depths, tiles and FP64 additions).
  *   stream     cudaStream_t (NULL: legacy default stream).
  *   sync       0: return after enqueueing; nonzero: wait for the stream and
  *              report a device-side timeout as JAC_ETIMEOUT.
  * The padded grid, (nz+2)*(ny+2)*row_pitch elements, must fit in
  * JAC_NOALLOC_SCRATCH_BYTES - 256 bytes (about 4.1 M FP64 or 8.4 M FP32 cells);
  * larger grids are rejected with JAC_EINVAL before anything runs.
- * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call before
- * any stream capture.  Every call shares the one scratch array, which keeps the
- * previous call's contents (each call re-initialises what it needs): calls
- * that can overlap on the GPU (different streams, or different threads) race,
- * so serialise them.
+ * First call on a device: it looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current), which is also when the
+ * driver commits the array's device memory (modules load lazily), so the first
+ * call does reserve JAC_NOALLOC_SCRATCH_BYTES on that device; make that first
+ * call before any stream capture.
+ * Timeouts: the status word is sticky.  A call with sync = 0 does not report a
+ * timeout of its own kernels; it stays recorded until the next call made with
+ * sync != 0, which returns JAC_ETIMEOUT and clears it.
+ * Every call shares the one scratch array, which keeps the previous call's
+ * contents (each call re-initialises what it needs): calls that can overlap on
+ * the GPU (different streams, or different threads) race, so serialise them.
  */
 #define JAC_NOALLOC_SCRATCH_BYTES (32u << 20)
 JAC_API int jacobi_sweep_noalloc(int nx, int ny, int nz, int dtype, void *grid,
@@ -296,6 +313,38 @@ JAC_API int jacobi_destroy(jacobi_t h);
 
 /* jacobi_strerror — static text for a status code. */
 JAC_API const char *jacobi_strerror(int code);
+
+/*
+ * jacobi_pipe_probe — measurement kernels for the roofline of the sweeps (no
+ * counterpart in the paper; the paper's own model, Sect. 1.3 Eq. 4-5, needs the
+ * machine's rates as inputs).  Launches `blocks` x `threads` threads (threads a
+ * multiple of 32, at most 256), each running JAC_PROBE_CHAINS independent
+ * dependency chains of `iters` operations of one kind from registers:
+ *   JAC_PROBE_DADD     FP64 additions (the FP64 unit)
+ *   JAC_PROBE_FADD     FP32 additions
+ *   JAC_PROBE_LOP3     3-input logic operations (the integer ALU pipe)
+ *   JAC_PROBE_IMAD     32-bit integer multiply-adds (the FMA pipe)
+ *   JAC_PROBE_EMU_ADD  exact binary64 additions on the integer pipes, the
+ *                      routine the FP64 sweeps use (see jacobi_emulated_add)
+ * so one launch performs blocks*threads*iters*JAC_PROBE_CHAINS operations; the
+ * caller times it (CUDA events).  out: device array of blocks*threads doubles
+ * that receives each thread's chain values.  Asynchronous on `stream`.
+ */
+#define JAC_PROBE_CHAINS 8
+enum jac_probe {
+    JAC_PROBE_DADD = 0,
+    JAC_PROBE_FADD = 1,
+    JAC_PROBE_LOP3 = 2,
+    JAC_PROBE_IMAD = 3,
+    JAC_PROBE_EMU_ADD = 4
+};
+JAC_API int jacobi_pipe_probe(int kind, double *out, int blocks, int threads, int iters,
+                              void *stream);
+
+/* jacobi_max_depth — the deepest temporal-blocking depth (Sect. 1.3) built for
+ * dtype and op (jac_op); every depth from 1 to it exists.  JAC_EINVAL for an
+ * unknown dtype or op; 0 when the operation has no kernel for the dtype. */
+JAC_API int jacobi_max_depth(int dtype, int op);
 
 /* jacobi_version — library version as 10000*major + 100*minor + patch. */
 JAC_API int jacobi_version(void);

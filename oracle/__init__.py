@@ -98,6 +98,21 @@ def sweeps(A, n, nx=None, dtype="f64", nthreads=1, lib=None):
     return B if in_b else A
 
 
+def sweeps_into(A, B, n, nx=None, dtype="f64", nthreads=1, lib=None):
+    """``n`` sweeps between the caller's arrays ``A`` (input) and ``B`` (whose
+    boundary layer must equal A's), without copying either; returns the array
+    that holds the result (A when n is even).  Used where the oracle is timed."""
+    lib = lib or load()
+    assert A.dtype == _DT[dtype] and B.dtype == A.dtype and A.shape == B.shape
+    assert A.flags["C_CONTIGUOUS"] and B.flags["C_CONTIGUOUS"]
+    nx = A.shape[2] - 2 if nx is None else nx
+    ny, nz, px, py = _dims(A, nx)
+    fn = {"f64": lib.oracle_sweeps_f64, "f32": lib.oracle_sweeps_f32,
+          "bf16": lib.oracle_sweeps_bf16}[dtype]
+    in_b = fn(_ptr(A), _ptr(B), nx, ny, nz, px, py, int(n), int(nthreads))
+    return B if in_b else A
+
+
 def rhs_sweeps(E, rho, n, nx=None, dtype="f32", nthreads=1, lib=None):
     """``n`` correction sweeps e' = (sum6(e) + rho) * RN(1/6) on a grid whose
     boundary layer is zero (the refinement's inner iteration)."""
@@ -189,5 +204,5 @@ def max_threads(lib=None):
     return (lib or load()).oracle_max_threads()
 
 
-__all__ = ["load", "sweeps", "rhs_sweeps", "residual_accumulate", "refine_solve",
+__all__ = ["load", "sweeps", "sweeps_into", "rhs_sweeps", "residual_accumulate", "refine_solve",
            "grad_f64", "f32_to_bf16", "bf16_to_f32", "max_threads"]

@@ -11,13 +11,17 @@ LIB_PATH = os.path.join(HERE, "libjacobi_gb300.so")
 JAC_OK, JAC_EINVAL, JAC_ENOMEM, JAC_ECUDA, JAC_ETIMEOUT, JAC_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 JAC_F64, JAC_F32, JAC_BF16 = 0, 1, 2
 JAC_KERNEL_AUTO, JAC_KERNEL_PLAIN, JAC_KERNEL_TB = 0, 1, 2
+JAC_OP_SWEEP, JAC_OP_RHS, JAC_OP_ADJOINT = 0, 1, 2
+JAC_PROBE_DADD, JAC_PROBE_FADD, JAC_PROBE_LOP3, JAC_PROBE_IMAD, JAC_PROBE_EMU_ADD = 0, 1, 2, 3, 4
+JAC_PROBE_CHAINS = 8
 
 EXPORTS = ["jacobi_create", "jacobi_sweep", "jacobi_sweep_ex", "jacobi_plan",
            "jacobi_sweep_rhs", "jacobi_residual_accumulate", "jacobi_adjoint",
            "jacobi_upload", "jacobi_download", "jacobi_check", "jacobi_destroy",
            "jacobi_strerror", "jacobi_version", "jacobi_sweep_noalloc",
            "jacobi_batch_create", "jacobi_batch_run", "jacobi_batch_info", "jacobi_batch_check",
-           "jacobi_batch_destroy", "jacobi_emulated_add", "jacobi_copy_planes"]
+           "jacobi_batch_destroy", "jacobi_emulated_add", "jacobi_copy_planes",
+           "jacobi_max_depth", "jacobi_pipe_probe"]
 
 JAC_BATCH_NO_GRAPH, JAC_BATCH_TEST_MISSING_PRODUCER = 1, 2
 
@@ -75,6 +79,8 @@ def load(path=None):
         "jacobi_batch_destroy": ([P], I),
         "jacobi_emulated_add": ([P, P, P, LL, P], I),
         "jacobi_copy_planes": ([P, P, LL, I, I, P], I),
+        "jacobi_max_depth": ([I, I], I),
+        "jacobi_pipe_probe": ([I, P, I, I, I, P], I),
     }
     for name, (args, res) in sig.items():
         f = getattr(lib, name)
@@ -151,6 +157,18 @@ def jacobi_check(h):
 
 def jacobi_destroy(h):
     _ck(load().jacobi_destroy(h), "jacobi_destroy")
+
+
+def jacobi_max_depth(dtype, op=JAC_OP_SWEEP):
+    rc = load().jacobi_max_depth(dtype, op)
+    if rc < 0:
+        raise JacobiError(rc, "jacobi_max_depth")
+    return rc
+
+
+def jacobi_pipe_probe(kind, out_ptr, blocks, threads, iters, stream):
+    _ck(load().jacobi_pipe_probe(kind, out_ptr, blocks, threads, iters, stream),
+        "jacobi_pipe_probe")
 
 
 def jacobi_version():

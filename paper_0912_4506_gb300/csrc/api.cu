@@ -13,13 +13,10 @@
 
 #include "../../include/jacobi.h"
 #include "launch.h"
+#include "plan.h"
 #include "tb.cuh"
 
 using namespace jac;
-
-namespace {
-constexpr int kDefaultF64Emu = 6;  // half additions per plane (3 of 5)
-}
 
 struct jacobi_s {
     int dtype;
@@ -40,203 +37,6 @@ struct jacobi_s {
 
 namespace {
 
-int elem_size(int dtype) { return dtype == JAC_F64 ? 8 : dtype == JAC_F32 ? 4 : 2; }
-
-int floor_div(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
-
-PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
-
-// 3D tensor map over the padded grid (nx+2, ny+2, nz+2) with a (bx, by, 1) box.
-// Elements outside the padded grid (including the row padding) read as zero.
-int make_map(CUtensorMap* map, const jacobi_s* h, void* base, int bx, int by) {
-    auto fn = encode_fn();
-    if (!fn) return JAC_ECUDA;
-    const int es = elem_size(h->dtype);
-    const CUtensorMapDataType dt = h->dtype == JAC_F64   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64
-                                   : h->dtype == JAC_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                                         : CU_TENSOR_MAP_DATA_TYPE_UINT16;
-    cuuint64_t dims[3] = {(cuuint64_t)h->g.nx + 2, (cuuint64_t)h->g.ny + 2,
-                          (cuuint64_t)h->g.nz + 2};
-    cuuint64_t strides[2] = {(cuuint64_t)h->g.px * es, (cuuint64_t)h->g.plane * es};
-    cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    CUresult r = fn(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? JAC_OK : JAC_ECUDA;
-}
-
-const std::vector<TBEntry>& tb_table(int dtype, int mode) {
-    static std::vector<TBEntry> tabs[3][3];
-    static std::once_flag once;
-    std::call_once(once, [] {
-        auto add = [](const TBEntry* p, int n) {
-            for (int i = 0; i < n; ++i) tabs[p[i].dtype][p[i].mode].push_back(p[i]);
-        };
-        int n;
-        const TBEntry* p;
-        p = tb_entries_f64(&n); add(p, n);
-        p = tb_entries_f32(&n); add(p, n);
-        p = tb_entries_f32_rhs(&n); add(p, n);
-        p = tb_entries_f32_adj(&n); add(p, n);
-        p = tb_entries_bf16(&n); add(p, n);
-        p = tb_entries_bf16_rhs(&n); add(p, n);
-        for (auto& d : tabs)
-            for (auto& v : d)
-                std::sort(v.begin(), v.end(),
-                          [](const TBEntry& x, const TBEntry& y) { return x.T < y.T; });
-    });
-    return tabs[dtype][mode];
-}
-
-// Allow every kernel of a table its dynamic shared memory on the current device
-// (needed before occupancy queries and launches; done once per device).
-void ensure_attrs(const std::vector<TBEntry>& tab, int device) {
-    static std::mutex mu;
-    static std::vector<std::pair<const void*, int>> done;
-    std::lock_guard<std::mutex> lock(mu);
-    for (const auto& e : tab) {
-        bool seen = false;
-        for (const auto& d : done)
-            if (d.first == e.kernel && d.second == device) seen = true;
-        if (seen) continue;
-        cudaFuncSetAttribute(e.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)e.smem);
-        done.emplace_back(e.kernel, device);
-    }
-}
-
-// Additions the FP64 plain sweep does on the integer pipes when the range check
-// allows it, in half additions per plane (0..8); JACOBI_F64_EMU overrides.
-int f64_emu_count() {
-    static int n = -1;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        n = kDefaultF64Emu;
-        if (const char* e = getenv("JACOBI_F64_EMU")) {
-            const int v = atoi(e);
-            if (v >= 0 && v <= 8) n = v;
-        }
-    });
-    return n;
-}
-
-const PlainEntry* plain_for(int dtype) {
-    if (dtype == JAC_F64) {
-        int n = 0;
-        const PlainEntry* tab = plain_entries_f64(&n);
-        const int want = f64_emu_count();
-        for (int i = 0; i < n; ++i)
-            if (tab[i].nemu == want) return &tab[i];
-        return plain_entry_f64();
-    }
-    return dtype == JAC_F32 ? plain_entry_f32() : plain_entry_bf16();
-}
-
-// Geometry of one temporally-blocked pass for an entry.
-struct TBGeom {
-    int ox, oy, x0_first, ntx, nty, kz, nchunk;
-    bool ok;
-};
-
-// Choose the number of k-chunks: enough CTAs to fill whole waves, but chunks
-// long enough that the 2T-plane pipeline fill/drain of each chunk stays small.
-int pick_chunks(int nz, int T, long long tiles, int slots) {
-    int best = 1;
-    double best_score = -1.0;
-    const int max_chunks = std::max(1, nz / std::max(4 * T, 8));
-    for (int c = 1; c <= max_chunks; ++c) {
-        const int kz = (nz + c - 1) / c;
-        const long long ctas = tiles * (long long)((nz + kz - 1) / kz);
-        const long long waves = (ctas + slots - 1) / slots;
-        const double fill = (double)ctas / (double)(waves * slots);
-        const double zeff = (double)kz / (double)(kz + 2 * T);
-        const double score = fill * zeff;
-        if (score > best_score + 1e-9) {
-            best_score = score;
-            best = c;
-        }
-    }
-    return best;
-}
-
-TBGeom tb_geom(const jacobi_s* h, const TBEntry& e) {
-    TBGeom r{};
-    const int A = 16 / elem_size(h->dtype);
-    const int EX = 32 * e.V, EY = e.NW, T = e.T;
-    r.ox = ((EX - 2 * T) / A) * A;
-    r.oy = EY - 2 * T;
-    r.ok = r.ox >= A && r.oy >= 1;
-    if (!r.ok) return r;
-    r.x0_first = floor_div(1 - T, A) * A;
-    r.ntx = (h->g.nx + 1 - (r.x0_first + T) + r.ox - 1) / r.ox;
-    r.nty = (h->g.ny + r.oy - 1) / r.oy;
-    int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, e.kernel, e.NW * 32, e.smem);
-    occ = std::max(occ, 1);
-    r.nchunk = pick_chunks(h->g.nz, T, (long long)r.ntx * r.nty, h->num_sms * occ);
-    r.kz = (h->g.nz + r.nchunk - 1) / r.nchunk;
-    r.nchunk = (h->g.nz + r.kz - 1) / r.kz;
-    return r;
-}
-
-int plain_chunks(const jacobi_s* h, const PlainEntry* pe, dim3* grid, int* kchunk) {
-    // interior-aligned kernels (V == 1, or FP64) start at x = 1; vector kernels at 0
-    const bool aligned_x1 = pe->V == 1 || h->dtype == JAC_F64;
-    const int nvec = aligned_x1 ? (h->g.nx + pe->V - 1) / pe->V : h->g.nx / pe->V + 1;
-    grid->x = (nvec + 31) / 32;
-    grid->y = (h->g.ny + pe->WY - 1) / pe->WY;
-    int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pe->kernel, 32 * pe->WY, 0);
-    occ = std::max(occ, 1);
-    const long long tiles = (long long)grid->x * grid->y;
-    const int c = pick_chunks(h->g.nz, 1, tiles, h->num_sms * occ);
-    *kchunk = (h->g.nz + c - 1) / c;
-    grid->z = (h->g.nz + *kchunk - 1) / *kchunk;
-    return JAC_OK;
-}
-
-// The pass depths for n sweeps at requested depth t with the available entries:
-// full passes of the deepest depth <= t, the remainder split greedily.
-bool split_passes(const std::vector<TBEntry>& tab, const jacobi_s* h, int n, int t,
-                  std::vector<int>* depths) {
-    std::vector<int> avail;
-    for (const auto& e : tab)
-        if (tb_geom(h, e).ok) avail.push_back(e.T);
-    if (avail.empty()) return false;
-    int tmax = 0;
-    for (int d : avail)
-        if (d <= t) tmax = std::max(tmax, d);
-    if (tmax == 0) tmax = avail.front();
-    int left = n;
-    while (left > 0) {
-        int d = 0;
-        for (int a : avail)
-            if (a <= std::min(left, tmax)) d = std::max(d, a);
-        if (d == 0) return false;
-        depths->push_back(d);
-        left -= d;
-    }
-    return true;
-}
-
-const TBEntry* find_entry(const std::vector<TBEntry>& tab, int T) {
-    for (const auto& e : tab)
-        if (e.T == T) return &e;
-    return nullptr;
-}
-
 int check_grid_args(int nx, int ny, int nz, int dtype, long long pitch) {
     if (nx < 1 || ny < 1 || nz < 1) return JAC_EINVAL;
     if (dtype < JAC_F64 || dtype > JAC_BF16) return JAC_EINVAL;
@@ -247,18 +47,6 @@ int check_grid_args(int nx, int ny, int nz, int dtype, long long pitch) {
 }
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
-
-// Depth used when the caller leaves it to the planner (t = 0), the fastest
-// measured at 512^3 on GB300: FP64 is bound by the FP64 pipe, so blocking cannot
-// help it (plain streaming kernel); plain FP32/bf16 sweeps peak at depth 3
-// (128 x 32 tiles), FP32 correction sweeps at 4 (tied with 3), bf16 correction
-// sweeps at 2, adjoint sweeps at 4.
-int default_t(int dtype, int mode) {
-    if (dtype == JAC_F64) return 1;
-    if (mode == MODE_PLAIN) return 3;
-    if (mode == MODE_RHS) return dtype == JAC_BF16 ? 2 : 4;
-    return 4;
-}
 
 // Run nsweeps of `mode` as a sequence of passes.  kernel: JAC_KERNEL_*.
 int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void* rho,
@@ -278,7 +66,7 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         const PlainEntry* pe = plain_for(h->dtype);
         dim3 grid;
         int kchunk = 0;
-        plain_chunks(h, pe, &grid, &kchunk);
+        plain_grid(pe, h->dtype, h->g, h->device, h->num_sms, &grid, &kchunk);
         if (info_only) {
             std::memset(info_only, 0, sizeof(*info_only));
             info_only->kernel = JAC_KERNEL_PLAIN;
@@ -314,21 +102,22 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         return JAC_OK;
     }
 
-    const auto& tab = tb_table(h->dtype, mode);
-    if (tab.empty()) return JAC_EUNSUPPORTED;
-    ensure_attrs(tab, h->device);
-    std::vector<int> depths;
-    if (nsweeps > 0 && !split_passes(tab, h, nsweeps, t, &depths)) return JAC_EUNSUPPORTED;
+    DepthPlan dp;
+    const int rc = plan_depths(h->dtype, mode, nsweeps, t, &dp);
+    if (rc != JAC_OK) return rc;
+    const long long slots_per_sm = h->num_sms;
 
     if (info_only) {
         std::memset(info_only, 0, sizeof(*info_only));
         info_only->kernel = JAC_KERNEL_TB;
-        info_only->passes = (int)depths.size();
-        if (!depths.empty()) {
-            const TBEntry* e = find_entry(tab, depths.front());
-            const TBGeom gm = tb_geom(h, *e);
-            info_only->t = depths.front();
-            info_only->remainder_t = depths.back() != depths.front() ? depths.back() : 0;
+        info_only->passes = dp.passes();
+        if (dp.passes() > 0) {
+            const int t0 = dp.depth(0);
+            const TBEntry* e = tb_entry(h->dtype, mode, t0);
+            const TileGeom gm = tile_geom(h->dtype, h->g, e->V, e->NW, e->T,
+                                          slots_per_sm * tb_occupancy(*e, h->device), 0);
+            info_only->t = t0;
+            info_only->remainder_t = dp.n_full > 0 ? dp.t_last : 0;
             info_only->tile_x = gm.ox;
             info_only->tile_y = gm.oy;
             info_only->ext_x = 32 * e->V;
@@ -339,19 +128,41 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
             info_only->grid_x = gm.ntx;
             info_only->grid_y = gm.nty;
             info_only->grid_z = gm.nchunk;
+            info_only->emu_adds = e->emu;
         }
         return JAC_OK;
     }
 
+    // FP64 blocked passes with integer-pipe additions: one range check per call
+    // (the sweep averages, so values stay in range for every later pass)
+    const int* fast = nullptr;
+    if (h->dtype == JAC_F64 && mode == MODE_PLAIN && dp.passes() > 0) {
+        bool any_emu = false;
+        for (int p = 0; p < 2; ++p) {
+            const int d = p == 0 ? dp.t_full : dp.t_last;
+            const TBEntry* e = d > 0 ? tb_entry(h->dtype, mode, d) : nullptr;
+            any_emu = any_emu || (e && e->emu > 0);
+        }
+        if (any_emu) {
+            fast = h->status + 16;
+            if (launch_range_check(static_cast<const double*>(h->a), h->g, h->status + 16,
+                                   h->stream) != cudaSuccess)
+                return JAC_ECUDA;
+        }
+    }
+
     int cur_b = 0;  // 0: current data in A
-    for (size_t p = 0; p < depths.size(); ++p) {
-        const TBEntry* e = find_entry(tab, depths[p]);
-        const TBGeom gm = tb_geom(h, *e);
+    for (int p = 0; p < dp.passes(); ++p) {
+        const TBEntry* e = tb_entry(h->dtype, mode, dp.depth(p));
+        if (!e) return JAC_EUNSUPPORTED;
+        const TileGeom gm = tile_geom(h->dtype, h->g, e->V, e->NW, e->T,
+                                      slots_per_sm * tb_occupancy(*e, h->device), 0);
         if (!gm.ok) return JAC_EUNSUPPORTED;
         const int EX = 32 * e->V, EY = e->NW;
         if (EX != h->map_box_x || EY != h->map_box_y) {
-            if (make_map(&h->map_a, h, h->a, EX, EY) != JAC_OK) return JAC_ECUDA;
-            if (make_map(&h->map_b, h, h->b, EX, EY) != JAC_OK) return JAC_ECUDA;
+            if (!encode_grid_map(&h->map_a, h->dtype, h->g, h->a, EX, EY) ||
+                !encode_grid_map(&h->map_b, h->dtype, h->g, h->b, EX, EY))
+                return JAC_ECUDA;
             h->map_box_x = EX;
             h->map_box_y = EY;
         }
@@ -363,10 +174,11 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         args.x0_first = gm.x0_first;
         args.kz = gm.kz;
         args.status = h->status;
+        args.fast = fast;
+        args.one = 1u;
         if (mode == MODE_RHS &&
             (rho != h->rho_ptr || EX != h->rho_box_x || EY != h->rho_box_y)) {
-            if (make_map(&h->map_rho, h, const_cast<void*>(rho), EX, EY) != JAC_OK)
-                return JAC_ECUDA;
+            if (!encode_grid_map(&h->map_rho, h->dtype, h->g, rho, EX, EY)) return JAC_ECUDA;
             h->rho_ptr = rho;
             h->rho_box_x = EX;
             h->rho_box_y = EY;
@@ -538,11 +350,20 @@ const char* jacobi_strerror(int code) {
         case JAC_ENOMEM: return "device allocation failed";
         case JAC_ECUDA: return "CUDA call failed";
         case JAC_ETIMEOUT: return "bounded device wait timed out";
-        case JAC_EUNSUPPORTED: return "no kernel for this dtype/mode/configuration";
+        case JAC_EUNSUPPORTED:
+            return "no kernel for this dtype/operation/depth (jacobi_max_depth gives the deepest "
+                   "depth built)";
         default: return "unknown status";
     }
 }
 
-int jacobi_version(void) { return 100; }
+int jacobi_max_depth(int dtype, int op) {
+    if (dtype < JAC_F64 || dtype > JAC_BF16 || op < JAC_OP_SWEEP || op > JAC_OP_ADJOINT)
+        return JAC_EINVAL;
+    const int mode = op == JAC_OP_SWEEP ? MODE_PLAIN : op == JAC_OP_RHS ? MODE_RHS : MODE_ADJ;
+    return max_depth(dtype, mode);
+}
+
+int jacobi_version(void) { return 200; }
 
 }  // extern "C"

@@ -26,6 +26,7 @@
 #include "../../include/jacobi.h"
 #include "batch_kernel.cuh"
 #include "launch.h"
+#include "plan.h"
 
 
 using namespace jac;
@@ -49,53 +50,19 @@ struct jacobi_batch_s {
 
 namespace {
 
-int bsize(int dtype) { return dtype == JAC_F64 ? 8 : dtype == JAC_F32 ? 4 : 2; }
-
-int floor_divb(int a, int b) { return (a >= 0) ? a / b : -((-a + b - 1) / b); }
-
-PFN_cuTensorMapEncodeTiled_v12000 batch_encoder() {
-    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void* p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
-                                             cudaEnableDefault, &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-    });
-    return fn;
-}
-
-bool batch_map(CUtensorMap* map, int dtype, const Geom& g, void* base) {
-    auto fn = batch_encoder();
-    if (!fn) return false;
-    const int es = bsize(dtype);
-    const CUtensorMapDataType dt = dtype == JAC_F32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
-                                                    : CU_TENSOR_MAP_DATA_TYPE_UINT16;
-    cuuint64_t dims[3] = {(cuuint64_t)g.nx + 2, (cuuint64_t)g.ny + 2, (cuuint64_t)g.nz + 2};
-    cuuint64_t strides[2] = {(cuuint64_t)g.px * es, (cuuint64_t)g.plane * es};
-    cuuint32_t box[3] = {32 * kBatchV, kBatchNW, 1};
-    cuuint32_t estr[3] = {1, 1, 1};
-    return fn(map, dt, 3, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// Tile geometry of a pass of depth t; the k-chunk count keeps chunks >= 8t planes.
+// Tile geometry of a pass of depth t; the k-chunk count keeps chunks >= 8t planes
+// (many grids share the GPU, so no grid needs whole waves of its own).
 BatchPassGeom pass_geom(const Geom& g, int dtype, int t, int nchunk_req) {
+    const int nchunk = nchunk_req > 0 ? nchunk_req : std::max(1, g.nz / std::max(8 * t, 32));
+    const TileGeom tg = tile_geom(dtype, g, kBatchV, kBatchNW, t, 1, nchunk);
     BatchPassGeom p{};
-    const int A = 16 / bsize(dtype);
-    const int EX = 32 * kBatchV, EY = kBatchNW;
     p.t = t;
-    p.ox = ((EX - 2 * t) / A) * A;
-    p.x0_first = floor_divb(1 - t, A) * A;
-    p.ntx = (g.nx + 1 - (p.x0_first + t) + p.ox - 1) / p.ox;
-    p.nty = (g.ny + (EY - 2 * t) - 1) / (EY - 2 * t);
-    int nchunk = nchunk_req > 0 ? nchunk_req : std::max(1, g.nz / std::max(8 * t, 32));
-    nchunk = std::min(nchunk, g.nz);
-    p.kz = (g.nz + nchunk - 1) / nchunk;
-    p.nchunk = (g.nz + p.kz - 1) / p.kz;
+    p.ox = tg.ox;
+    p.x0_first = tg.x0_first;
+    p.ntx = tg.ntx;
+    p.nty = tg.nty;
+    p.kz = tg.kz;
+    p.nchunk = tg.nchunk;
     return p;
 }
 
@@ -138,7 +105,7 @@ int jacobi_batch_create(jacobi_batch_t* out, int count, const int* dims,
     if (count < 1 || !dims || !pitches || !grids_a || !grids_b || !nsweeps) return JAC_EINVAL;
     if (dtype != JAC_F32 && dtype != JAC_BF16) return JAC_EUNSUPPORTED;
     if (flags & ~(JAC_BATCH_NO_GRAPH | JAC_BATCH_TEST_MISSING_PRODUCER)) return JAC_EINVAL;
-    const int es = bsize(dtype);
+    const int es = elem_size(dtype);
     jacobi_batch_s* b = new (std::nothrow) jacobi_batch_s();
     if (!b) return JAC_ENOMEM;
     b->count = count;
@@ -169,7 +136,11 @@ int jacobi_batch_create(jacobi_batch_t* out, int count, const int* dims,
             return JAC_EINVAL;
         }
         Geom g{nx, ny, nz, px, px * (ny + 2)};
-        int ti = (t && t[i] > 0) ? std::min(t[i], kBatchTMax) : 4;
+        if (t && t[i] > kBatchTMax) {
+            delete b;
+            return JAC_EUNSUPPORTED;  // deeper than the batched kernel's deepest depth
+        }
+        int ti = (t && t[i] > 0) ? t[i] : 4;
         ti = std::min(ti, std::max(1, nsweeps[i]));
         const int nc = nchunk ? nchunk[i] : 0;
         BatchGridDesc& d = b->host_desc[i];
@@ -185,8 +156,8 @@ int jacobi_batch_create(jacobi_batch_t* out, int count, const int* dims,
         b->t_used[i] = ti;
         b->passes[i] = d.npass;
         max_pass = std::max(max_pass, d.npass);
-        if (!batch_map(&maps[2 * i], dtype, g, grids_a[i]) ||
-            !batch_map(&maps[2 * i + 1], dtype, g, grids_b[i])) {
+        if (!encode_grid_map(&maps[2 * i], dtype, g, grids_a[i], 32 * kBatchV, kBatchNW) ||
+            !encode_grid_map(&maps[2 * i + 1], dtype, g, grids_b[i], 32 * kBatchV, kBatchNW)) {
             delete b;
             return JAC_ECUDA;
         }

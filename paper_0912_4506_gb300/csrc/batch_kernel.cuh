@@ -97,6 +97,8 @@ __global__ void __launch_bounds__(kBatchNW * 32, 1) tb_batch_kernel(const BatchA
         a.x0_first = pg.x0_first;
         a.kz = pg.kz;
         a.status = ba.status;
+        a.fast = nullptr;
+        a.one = 1u;
         const int bx = item.tile % pg.ntx;
         const int by = (item.tile / pg.ntx) % pg.nty;
         const int bz = item.tile / (pg.ntx * pg.nty);

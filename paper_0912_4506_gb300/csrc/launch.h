@@ -26,6 +26,7 @@ struct TBEntry {
     int T;          // temporal-blocking depth
     int NS;         // TMA ring slots
     size_t smem;    // dynamic shared memory bytes
+    int emu;        // FP64: additions on the integer pipes when the range check passes
     TBLaunchFn launch;
     const void* kernel;
 };
@@ -44,6 +45,8 @@ struct PlainEntry {
 
 // Tables provided by the per-dtype translation units.
 const TBEntry* tb_entries_f64(int* n);
+const TBEntry* tb_entries_f64_deep(int* n);
+const TBEntry* tb_entries_f64_adj(int* n);
 const TBEntry* tb_entries_f32(int* n);
 const TBEntry* tb_entries_f32_rhs(int* n);
 const TBEntry* tb_entries_f32_adj(int* n);

@@ -42,6 +42,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "emu.cuh"
 
 namespace jac {
 
@@ -57,6 +58,8 @@ struct TBArgs {
     int x0_first;       // x origin of tile 0's extended tile (aligned, may be < 0)
     int kz;             // output k-planes per CTA
     int* status;        // device status word (timeouts)
+    const int* fast;    // FP64 (EMU > 0): range flag set by range_check_kernel, or null
+    uint32_t one;       // a runtime 1 (the integer-pipe additions' multiplier)
 };
 
 // Shared memory of one CTA: mbarriers (HEADER), the TMA ring (NS planes), the
@@ -93,7 +96,10 @@ using IC = std::integral_constant<int, N>;
 // One output tile of one temporally-blocked pass.  `smem` is the CTA's dynamic
 // shared memory (TBLayout), `s_abort` a shared flag.  Returns false when a TMA
 // wait timed out (status already recorded).  All threads of the CTA call it.
-template <class Tr, int V, int NW, int T, int MODE, bool FAST>
+// EMU (FP64 only): the first EMU of the five additions of every update run as
+// exact binary64 additions on the integer pipes (emu.cuh), valid when every
+// value of the pass lies in [2^-1000, 2^1000]; the results are the same bits.
+template <class Tr, int V, int NW, int T, int MODE, bool FAST, int EMU = 0>
 __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorMap* tmap_rho,
                                         const TBArgs& a, int bx, int by, int bz,
                                         unsigned char* smem, int* s_abort) {
@@ -218,6 +224,16 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
         }
     };
 
+    // addition number idx (0..4) of an update: the first EMU on the integer pipes
+    const uint32_t one = a.one;
+    auto add = [one](int idx, C x, C y) -> C {
+        if constexpr (EMU > 0 && std::is_same<C, double>::value) {
+            if (idx < EMU) return add_pos_exact_f(x, y, one);
+        }
+        return Tr::add(x, y);
+    };
+    (void)one;
+
     int cur_m = 0;  // step being executed (for the clean-up after a timeout)
     int rs = 0;     // rho slot of plane Zlo + m (MODE_RHS)
     // One step of the k-march; PH = m mod 6 fixes slot, parity and rotation.
@@ -266,11 +282,11 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
                 for (int e = 0; e < V; ++e) {
                     const C l = (e == 0) ? left : r[s - 1][CUR][e - 1];
                     const C rr = (e == V - 1) ? right : r[s - 1][CUR][e + 1];
-                    C sum = Tr::add(l, rr);
-                    sum = Tr::add(sum, Tr::ld(vn.v[e]));
-                    sum = Tr::add(sum, Tr::ld(vs.v[e]));
-                    sum = Tr::add(sum, r[s - 1][OLD][e]);
-                    sum = Tr::add(sum, r[s - 1][NEW][e]);
+                    C sum = add(0, l, rr);
+                    sum = add(1, sum, Tr::ld(vn.v[e]));
+                    sum = add(2, sum, Tr::ld(vs.v[e]));
+                    sum = add(3, sum, r[s - 1][OLD][e]);
+                    sum = add(4, sum, r[s - 1][NEW][e]);
                     if (MODE == MODE_RHS) sum = Tr::add(sum, Tr::ld(vr.v[e]));
                     val[e] = Tr::mul(sum, c6);
                 }
@@ -377,7 +393,10 @@ __device__ __forceinline__ bool tile_inside_xy(const TBArgs& a, int bx, int by) 
     return X0 >= 1 && X0 + 32 * V - 1 <= a.g.nx && Y0 >= 1 && Y0 + NW - 1 <= a.g.ny;
 }
 
-template <class Tr, int V, int NW, int T, int MODE, int NS>
+// EMU > 0 (FP64 plain sweeps): the variant with integer-pipe additions runs when
+// the call's range check passed (a.fast set), else every addition stays on the
+// FP64 unit; both give the same bits.
+template <class Tr, int V, int NW, int T, int MODE, int NS, int EMU = 0>
 __global__ void __launch_bounds__(NW * 32, 1)
     tb_sweep_kernel(const __grid_constant__ CUtensorMap tmap,
                     const __grid_constant__ CUtensorMap tmap_rho, const TBArgs a) {
@@ -390,7 +409,19 @@ __global__ void __launch_bounds__(NW * 32, 1)
         if (MODE == MODE_RHS) prefetch_tmap(&tmap_rho);
     }
     const int bx = blockIdx.x, by = blockIdx.y, bz = blockIdx.z;
-    if (tile_inside_xy<V, NW, T>(a, bx, by))
+    const bool inside = tile_inside_xy<V, NW, T>(a, bx, by);
+    if constexpr (EMU > 0) {
+        if (a.fast != nullptr && *a.fast) {
+            if (inside)
+                tb_tile<Tr, V, NW, T, MODE, true, EMU>(&tmap, &tmap_rho, a, bx, by, bz, smem,
+                                                       &s_abort);
+            else
+                tb_tile<Tr, V, NW, T, MODE, false, EMU>(&tmap, &tmap_rho, a, bx, by, bz, smem,
+                                                        &s_abort);
+            return;
+        }
+    }
+    if (inside)
         tb_tile<Tr, V, NW, T, MODE, true>(&tmap, &tmap_rho, a, bx, by, bz, smem, &s_abort);
     else
         tb_tile<Tr, V, NW, T, MODE, false>(&tmap, &tmap_rho, a, bx, by, bz, smem, &s_abort);

@@ -1,13 +1,15 @@
-// FP64 kernels: plain streaming sweep, temporally-blocked sweep, adjoint sweep.
+// FP64 kernels: plain streaming sweep and temporally-blocked sweep.  The blocked
+// sweep carries the integer-pipe additions (3 of the 5 additions of an update,
+// valid when the call's range check passes), like the plain sweep.
 #include "tb_inst.cuh"
 
 namespace jac {
 
+// Extended tiles 64 x 32 (depths 1-2) and 64 x 24 (depths 3-4): the tallest
+// whose registers fit without spills; depths 5-8 are in tb_f64_deep.cu.
 static const TBEntry kTB[] = {
-    JAC_TB(F64, 2, 16, 1, MODE_PLAIN, 6), JAC_TB(F64, 2, 16, 2, MODE_PLAIN, 6),
-    JAC_TB(F64, 2, 16, 3, MODE_PLAIN, 6), JAC_TB(F64, 2, 16, 4, MODE_PLAIN, 6),
-    JAC_TB(F64, 2, 16, 1, MODE_ADJ, 6),   JAC_TB(F64, 2, 16, 2, MODE_ADJ, 6),
-    JAC_TB(F64, 2, 16, 3, MODE_ADJ, 6),   JAC_TB(F64, 2, 16, 4, MODE_ADJ, 6),
+    JAC_TBE(F64, 2, 32, 1, MODE_PLAIN, 6, 3), JAC_TBE(F64, 2, 32, 2, MODE_PLAIN, 6, 3),
+    JAC_TBE(F64, 2, 24, 3, MODE_PLAIN, 6, 3), JAC_TBE(F64, 2, 24, 4, MODE_PLAIN, 6, 3),
 };
 JAC_TABLE(tb_entries_f64, kTB)
 

@@ -12,11 +12,11 @@ constexpr size_t tb_smem_bytes() {
     return TBLayout<V, NW, T, NS, typename TR::S, rho_slots<MODE, NS, T>()>::bytes();
 }
 
-template <class TR, int V, int NW, int T, int MODE, int NS>
+template <class TR, int V, int NW, int T, int MODE, int NS, int EMU>
 cudaError_t tb_launch(const CUtensorMap& map, const CUtensorMap& map_rho, const TBArgs& a,
                       dim3 grid, cudaStream_t st) {
     constexpr size_t smem = tb_smem_bytes<TR, V, NW, T, MODE, NS>();
-    tb_sweep_kernel<TR, V, NW, T, MODE, NS><<<grid, NW * 32, smem, st>>>(map, map_rho, a);
+    tb_sweep_kernel<TR, V, NW, T, MODE, NS, EMU><<<grid, NW * 32, smem, st>>>(map, map_rho, a);
     return cudaGetLastError();
 }
 
@@ -31,10 +31,12 @@ cudaError_t plain_launch(const void* A, void* B, const Geom& g, int kchunk, dim3
 
 }  // namespace jac
 
-#define JAC_TB(TR, V, NW, T, MODE, NS)                                         \
-    {TR::kDtype, MODE, V, NW, T, NS, ::jac::tb_smem_bytes<TR, V, NW, T, MODE, NS>(), \
-     &::jac::tb_launch<TR, V, NW, T, MODE, NS>,                               \
-     reinterpret_cast<const void*>(&::jac::tb_sweep_kernel<TR, V, NW, T, MODE, NS>)}
+#define JAC_TBE(TR, V, NW, T, MODE, NS, EMU)                                          \
+    {TR::kDtype, MODE, V, NW, T, NS, ::jac::tb_smem_bytes<TR, V, NW, T, MODE, NS>(), EMU, \
+     &::jac::tb_launch<TR, V, NW, T, MODE, NS, EMU>,                                \
+     reinterpret_cast<const void*>(&::jac::tb_sweep_kernel<TR, V, NW, T, MODE, NS, EMU>)}
+
+#define JAC_TB(TR, V, NW, T, MODE, NS) JAC_TBE(TR, V, NW, T, MODE, NS, 0)
 
 #define JAC_PLAIN(TR, V, WY, NEMU) \
     {TR::kDtype, V, WY, NEMU, &::jac::plain_launch<TR, V, WY, NEMU>, \

@@ -66,3 +66,18 @@ def test_missing_library_fails_loudly(tmp_path):
     from paper_0912_4506_gb300 import _lib
     with pytest.raises(RuntimeError, match="CUDA library missing"):
         _lib.load(str(tmp_path / "libjacobi_gb300.so"))
+
+
+def test_max_depth_without_device(lib):
+    """The deepest depth per dtype and operation comes from the kernel tables (no
+    device call): every depth from 1 up to it exists."""
+    from paper_0912_4506_gb300 import _lib
+    want = {(_lib.JAC_F64, _lib.JAC_OP_SWEEP): 8, (_lib.JAC_F32, _lib.JAC_OP_SWEEP): 8,
+            (_lib.JAC_BF16, _lib.JAC_OP_SWEEP): 8, (_lib.JAC_F32, _lib.JAC_OP_RHS): 6,
+            (_lib.JAC_BF16, _lib.JAC_OP_RHS): 6, (_lib.JAC_F64, _lib.JAC_OP_RHS): 0,
+            (_lib.JAC_F32, _lib.JAC_OP_ADJOINT): 4, (_lib.JAC_F64, _lib.JAC_OP_ADJOINT): 4,
+            (_lib.JAC_BF16, _lib.JAC_OP_ADJOINT): 0}
+    for (dt, op), mt in want.items():
+        assert lib.jacobi_max_depth(dt, op) == mt, (dt, op)
+    assert lib.jacobi_max_depth(3, 0) == _lib.JAC_EINVAL
+    assert lib.jacobi_max_depth(0, 3) == _lib.JAC_EINVAL

@@ -86,6 +86,47 @@ def test_sweep_with_negative_values_uses_fp64_unit_and_stays_exact():
     assert np.array_equal(got, oracle.sweeps(u0, 9, nx=nx)[:, :, :nx + 2])
 
 
+def _wide_range_grid(nx, ny, nz, seed):
+    """Positive normal values spread over 2^-60 .. 1 (log-uniform): the range
+    check passes, and many additions meet exponent gaps above 31, which the
+    integer path hands to the FP64 unit lane by lane."""
+    from paper_0912_4506_gb300 import inputs
+    px = inputs.row_pitch(nx, "f64")
+    rng = np.random.default_rng(seed)
+    a = np.zeros((nz + 2, ny + 2, px))
+    a[:, :, :nx + 2] = 2.0 ** (-60.0 * rng.random((nz + 2, ny + 2, nx + 2)))
+    return a
+
+
+@pytest.mark.parametrize("t", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_blocked_fp64_integer_pipe_adds_every_depth(t):
+    """FP64 blocked passes with 3 of the 5 additions on the integer pipes: bit-exact
+    at every depth on uniform data and on data with a wide exponent range."""
+    from paper_0912_4506_gb300 import api
+    for a, nx in ((make_grid(70, 45, 23, "f64"), 70), (_wide_range_grid(53, 40, 19, 4), 53)):
+        j = api.Jacobi(api.as_grid(to_dev(a, "f64"), nx))
+        assert j.plan(11, t, api.JAC_KERNEL_TB)["emu_adds"] == 3
+        got = to_host(j.sweep(11, t, api.JAC_KERNEL_TB), "f64")
+        j.check()
+        j.close()
+        want = oracle.sweeps(a, 11, nx=nx)[:, :, :nx + 2]
+        assert np.array_equal(got, want), t
+
+
+def test_blocked_fp64_zero_and_negative_values_use_fp64_unit():
+    """Values outside [2^-1000, 2^1000] (zeros, negatives) fail the range check, so
+    the blocked FP64 pass keeps every addition on the FP64 unit: still bit-exact."""
+    from paper_0912_4506_gb300 import api, inputs
+    nx, ny, nz = 40, 33, 21
+    u0 = inputs.laplace_boundary_f64(nx, ny, nz, px=inputs.row_pitch(nx, "f64"))
+    u0[1:-1, 1:-1, 1:nx + 1] = np.random.default_rng(3).random((nz, ny, nx)) - 0.5
+    for t in (2, 4, 8):
+        j = api.Jacobi(api.as_grid(to_dev(u0, "f64"), nx))
+        got = to_host(j.sweep(9, t, api.JAC_KERNEL_TB), "f64")
+        j.close()
+        assert np.array_equal(got, oracle.sweeps(u0, 9, nx=nx)[:, :, :nx + 2]), t
+
+
 @pytest.mark.parametrize("nemu", [0, 2, 4, 5, 6, 7, 8])
 def test_every_emulation_split_bit_exact(nemu, monkeypatch):
     """Run each split in a fresh process (the split is read once per process)."""

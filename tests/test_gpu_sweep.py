@@ -43,7 +43,7 @@ def test_plain_kernel_bit_exact(shape, dtype):
         assert first_diff(got, want) is None, (n, first_diff(got, want))
 
 
-TMAX = {"f64": 4, "f32": 8, "bf16": 8}
+TMAX = {"f64": 8, "f32": 8, "bf16": 8}
 
 
 @pytest.mark.parametrize("shape", SHAPES, ids=lambda s: "x".join(map(str, s)))
@@ -74,8 +74,29 @@ def test_config_64cubed_fp64_100_sweeps():
     a = make_grid(64, 64, 64, "f64")
     want = oracle_sweeps(a, 100, 64, "f64")
     assert first_diff(run_gpu(a, 100, 1, PLAIN, "f64", 64), want) is None
-    for t in (1, 2, 3, 4, 8, 16):
+    for t in (1, 2, 3, 4, 8):
         assert first_diff(run_gpu(a, 100, t, TB, "f64", 64), want) is None, t
+    _assert_depth_rejected(a, 16, "f64", 64)
+
+
+def _assert_depth_rejected(a, t, dtype, nx):
+    """A depth deeper than the deepest kernel built is rejected before any launch
+    (no silent clamping), and the plan query says the same."""
+    from paper_0912_4506_gb300 import _lib, api
+    j = api.Jacobi(api.as_grid(to_dev(a, dtype), nx))
+    before = to_host(j.A, dtype)
+    for call in (lambda: j.sweep(100, t, TB), lambda: j.plan(100, t, TB)):
+        with pytest.raises(_lib.JacobiError) as ei:
+            call()
+        assert ei.value.code == _lib.JAC_EUNSUPPORTED
+    assert np.array_equal(to_host(j.A, dtype), before)
+    j.close()
+
+
+def test_max_depth_matches_tables():
+    from paper_0912_4506_gb300 import _lib
+    for dtype, code in (("f64", _lib.JAC_F64), ("f32", _lib.JAC_F32), ("bf16", _lib.JAC_BF16)):
+        assert _lib.jacobi_max_depth(code, _lib.JAC_OP_SWEEP) == TMAX[dtype]
 
 
 @pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
@@ -130,9 +151,22 @@ def _oracle_512():
 @pytest.mark.parametrize("t,kernel", [(1, PLAIN), (1, TB), (2, TB), (4, TB), (8, TB),
                                       (16, TB)])
 def test_full_size_512cubed_fp64(t, kernel):
-    """512^3 FP64, 100 sweeps, the benchmark's launch configuration: every output
-    cell compared with the (OpenMP, bit-identical) oracle."""
+    """512^3 FP64, 100 sweeps, the benchmark's launch configuration and the depths
+    t in {1, 2, 4, 8, 16} of the workload: every output cell compared with the
+    (OpenMP, bit-identical) oracle.  Depth 16 has no kernel (an extended tile needs
+    more than 32 rows); the call must say so instead of running another depth."""
     a, want = _oracle_512()
+    if t == 16:
+        _assert_depth_rejected(a, t, "f64", 512)
+        return
+    from paper_0912_4506_gb300 import api
+    A = api.as_grid(to_dev(a, "f64"), 512)
+    j = api.Jacobi(A)
+    plan = j.plan(100, t, kernel)
+    assert plan["t"] == t
+    if kernel == TB:
+        assert plan["emu_adds"] == 3  # the integer-pipe additions are in use
+    j.close()
     got = run_gpu(a, 100, t, kernel, "f64", 512)
     assert first_diff(got, want) is None, (t, first_diff(got, want))
 

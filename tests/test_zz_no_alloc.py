@@ -1,9 +1,11 @@
 """jacobi_sweep_noalloc: the sweep for callers that cannot allocate device memory
 (code that runs where cudaMalloc is not allowed or not wanted, e.g. a host
-framework that owns all device memory through its own pool).  Called through the
-C ABI, it must give the same grid as the handle-based jacobi_sweep (the
-library's sweeps are bit-exact, so the tolerance is zero), on two calls in a row
-that share the library's static scratch array.  This file is collected last on
+framework that owns all device memory through its own pool, or a plug-in that
+must not grow the process's device footprint).  Called through the C ABI, it
+must give the same grid as the handle-based jacobi_sweep (the library's sweeps
+are bit-exact, so the tolerance is zero), on two calls in a row that share the
+library's static scratch array, and a call after the first one on the device
+must leave the free device memory unchanged.  This file is collected last on
 purpose: it must pass alone in a fresh process and after every other test."""
 import ctypes
 
@@ -64,3 +66,22 @@ def test_noalloc_rejects_grid_larger_than_scratch():
                                   ctypes.c_void_p(small.data_ptr()), 258, 1, 0, None, 1)
     assert rc == _lib.JAC_EINVAL
     assert b"invalid" in lib.jacobi_strerror(rc)
+
+
+@pytest.mark.parametrize("dtype,t", [("f64", 0), ("f64", 4), ("f32", 3), ("bf16", 2)])
+def test_noalloc_call_reserves_no_device_memory(dtype, t):
+    """After a first call of the same kind (which loads the kernels and commits the
+    scratch array), a further call leaves the device's free memory unchanged."""
+    import torch
+    nx, ny, nz = 48, 40, 30
+    a = make_grid(nx, ny, nz, dtype)
+    _via_noalloc(a, nx, dtype, 7, t)  # first call: kernels and scratch array loaded
+    full = to_dev(a, dtype)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    from paper_0912_4506_gb300 import _lib
+    code = {"f64": _lib.JAC_F64, "f32": _lib.JAC_F32, "bf16": _lib.JAC_BF16}[dtype]
+    _lib.jacobi_sweep_noalloc(nx, ny, nz, code, full.data_ptr(), full.shape[2], 7, t,
+                              torch.cuda.current_stream().cuda_stream, 1)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0

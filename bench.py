@@ -36,15 +36,13 @@ ALGO_BYTES_PER_LUP = {"f64": 16, "f32": 8, "bf16": 4}
 # kernel on a 384^3 grid (dram__bytes_read.sum + dram__bytes_write.sum), scaled
 # to 512^3 by the lattice-site updates (traffic is proportional to them: 16 B per
 # update, no re-reads).  A kernel without a capture of its current code: None.
-TRAFFIC_PER_LAUNCH = {
-    "plain_sweep_kernel<F64,emu=6>": round((489529856 + 410431232) * (512 / 384) ** 3),
-}
+TRAFFIC_PER_LAUNCH = {}
 
 # Pipe-rate probes (jacobi_pipe_probe): launch shape and operations per update of
 # the FP64 sweep with 3 of its 5 additions on the integer pipes.
 PROBE_BLOCKS_PER_SM, PROBE_THREADS = 8, 256
-F64_UNIT_OPS_PER_LUP = {"all_fp64": 6, "emu3": 3}   # FP64-unit operations per update
-EMU_ADDS_PER_LUP = 3
+F64_UNIT_OPS_PER_LUP = {"all_fp64": 6, "acc4": 2}   # FP64-unit operations per update
+ACC_ADDS_PER_LUP = 4                                 # additions through the accumulator
 
 
 def parse():
@@ -221,8 +219,9 @@ def measure_pipes(dev):
     res = {}
     kinds = {"dadd": _lib.JAC_PROBE_DADD, "fadd": _lib.JAC_PROBE_FADD,
              "lop3": _lib.JAC_PROBE_LOP3, "imad": _lib.JAC_PROBE_IMAD,
-             "emu_add": _lib.JAC_PROBE_EMU_ADD}
-    iters = {"dadd": 2048, "fadd": 16384, "lop3": 8192, "imad": 8192, "emu_add": 1024}
+             "emu_add": _lib.JAC_PROBE_EMU_ADD, "acc_add": _lib.JAC_PROBE_ACC_ADD}
+    iters = {"dadd": 2048, "fadd": 16384, "lop3": 8192, "imad": 8192, "emu_add": 1024,
+             "acc_add": 2048}
     for name, kind in kinds.items():
         it = iters[name]
         _lib.jacobi_pipe_probe(kind, out.data_ptr(), blocks, PROBE_THREADS, it,
@@ -580,9 +579,9 @@ def run_ours(args):
     fp64_only = pipes["dadd_gops"] / F64_UNIT_OPS_PER_LUP["all_fp64"]
     pipes["fp64_unit_only_ceiling_glups"] = round(fp64_only, 2)
     pipes["frac_vs_fp64_unit_only"] = round(achieved_glups / fp64_only, 4)
-    if emu > 0 and plan["kernel"] == 1 and emu == 6:
-        mix = min(pipes["dadd_gops"] / F64_UNIT_OPS_PER_LUP["emu3"],
-                  pipes["emu_add_gops"] / EMU_ADDS_PER_LUP)
+    if plan["kernel"] == 1 and emu == 2 * ACC_ADDS_PER_LUP:
+        mix = min(pipes["dadd_gops"] / F64_UNIT_OPS_PER_LUP["acc4"],
+                  pipes["acc_add_gops"] / ACC_ADDS_PER_LUP)
         pipes["kernel_mix_ceiling_glups"] = round(mix, 2)
         pipes["frac_vs_kernel_mix"] = round(achieved_glups / mix, 4)
     pipes["hbm_ceiling_glups"] = round(pk["hbm_gbs"] / ALGO_BYTES_PER_LUP["f64"], 2)

@@ -89,9 +89,10 @@ typedef struct {
     int threads;           /* threads per CTA                                     */
     int smem_bytes;        /* dynamic shared memory per CTA                       */
     int grid_x, grid_y, grid_z;
-    int emu_adds;          /* FP64 plain sweep: additions done on the integer pipes
-                              when the grid's values allow it (see jacobi_emulated_add),
-                              in half additions per plane: 5 = 2 and 3 on alternate planes */
+    int emu_adds;          /* FP64 sweeps: additions done on the integer pipes when
+                              the grid's values allow it (see jacobi_emulated_add and
+                              jacobi_emulated_sum6), in half additions per update:
+                              5 = 2 and 3 on alternate planes, 8 = 4 of the 5 */
 } jacobi_plan_info;
 
 /*
@@ -293,6 +294,19 @@ JAC_API int jacobi_emulated_add(const double *a, const double *b, double *out, l
                                 void *stream);
 
 /*
+ * jacobi_emulated_sum6 — out[i] = ((((x0 + x1) + x2) + x3) + x4) + x5 with
+ * x_j = x[j*n + i], each addition rounded to nearest even in binary64 (the
+ * partial sums of Eq. 1), computed the way the FP64 sweeps compute them: an
+ * unpacked running sum on the integer pipes, and the FP64 unit for every warp
+ * that holds an operand which is not a positive normal double or an exponent gap
+ * outside that routine's window.  The results equal the FP64 unit's sequential
+ * sums bit for bit; this entry point lets tests check that on any set of
+ * 6-tuples.  x: device array of 6*n doubles, out: n doubles; asynchronous on
+ * `stream`.
+ */
+JAC_API int jacobi_emulated_sum6(const double *x, double *out, long long n, void *stream);
+
+/*
  * jacobi_copy_planes — copy nplanes consecutive k-planes of one padded grid into
  * another of the same row pitch and ny (plane size plane_elems = row_pitch*(ny+2)
  * elements of elem_bytes each): the halo exchange of the z-slab decomposition
@@ -324,8 +338,10 @@ JAC_API const char *jacobi_strerror(int code);
  *   JAC_PROBE_FADD     FP32 additions
  *   JAC_PROBE_LOP3     3-input logic operations (the integer ALU pipe)
  *   JAC_PROBE_IMAD     32-bit integer multiply-adds (the FMA pipe)
- *   JAC_PROBE_EMU_ADD  exact binary64 additions on the integer pipes, the
- *                      routine the FP64 sweeps use (see jacobi_emulated_add)
+ *   JAC_PROBE_EMU_ADD  exact binary64 additions on the integer pipes, one
+ *                      packed addition at a time (see jacobi_emulated_add)
+ *   JAC_PROBE_ACC_ADD  additions to the unpacked exact running sum the FP64
+ *                      sweeps use (see jacobi_emulated_sum6)
  * so one launch performs blocks*threads*iters*JAC_PROBE_CHAINS operations; the
  * caller times it (CUDA events).  out: device array of blocks*threads doubles
  * that receives each thread's chain values.  Asynchronous on `stream`.
@@ -336,7 +352,8 @@ enum jac_probe {
     JAC_PROBE_FADD = 1,
     JAC_PROBE_LOP3 = 2,
     JAC_PROBE_IMAD = 3,
-    JAC_PROBE_EMU_ADD = 4
+    JAC_PROBE_EMU_ADD = 4,
+    JAC_PROBE_ACC_ADD = 5
 };
 JAC_API int jacobi_pipe_probe(int kind, double *out, int blocks, int threads, int iters,
                               void *stream);

@@ -13,6 +13,7 @@ JAC_F64, JAC_F32, JAC_BF16 = 0, 1, 2
 JAC_KERNEL_AUTO, JAC_KERNEL_PLAIN, JAC_KERNEL_TB = 0, 1, 2
 JAC_OP_SWEEP, JAC_OP_RHS, JAC_OP_ADJOINT = 0, 1, 2
 JAC_PROBE_DADD, JAC_PROBE_FADD, JAC_PROBE_LOP3, JAC_PROBE_IMAD, JAC_PROBE_EMU_ADD = 0, 1, 2, 3, 4
+JAC_PROBE_ACC_ADD = 5
 JAC_PROBE_CHAINS = 8
 
 EXPORTS = ["jacobi_create", "jacobi_sweep", "jacobi_sweep_ex", "jacobi_plan",
@@ -21,7 +22,7 @@ EXPORTS = ["jacobi_create", "jacobi_sweep", "jacobi_sweep_ex", "jacobi_plan",
            "jacobi_strerror", "jacobi_version", "jacobi_sweep_noalloc",
            "jacobi_batch_create", "jacobi_batch_run", "jacobi_batch_info", "jacobi_batch_check",
            "jacobi_batch_destroy", "jacobi_emulated_add", "jacobi_copy_planes",
-           "jacobi_max_depth", "jacobi_pipe_probe"]
+           "jacobi_max_depth", "jacobi_pipe_probe", "jacobi_emulated_sum6"]
 
 JAC_BATCH_NO_GRAPH, JAC_BATCH_TEST_MISSING_PRODUCER = 1, 2
 
@@ -80,6 +81,7 @@ def load(path=None):
         "jacobi_emulated_add": ([P, P, P, LL, P], I),
         "jacobi_copy_planes": ([P, P, LL, I, I, P], I),
         "jacobi_max_depth": ([I, I], I),
+        "jacobi_emulated_sum6": ([P, P, LL, P], I),
         "jacobi_pipe_probe": ([I, P, I, I, I, P], I),
     }
     for name, (args, res) in sig.items():
@@ -228,6 +230,10 @@ def jacobi_batch_destroy(h):
 
 def jacobi_emulated_add(a_ptr, b_ptr, out_ptr, n, stream):
     _ck(load().jacobi_emulated_add(a_ptr, b_ptr, out_ptr, n, stream), "jacobi_emulated_add")
+
+
+def jacobi_emulated_sum6(x_ptr, out_ptr, n, stream):
+    _ck(load().jacobi_emulated_sum6(x_ptr, out_ptr, n, stream), "jacobi_emulated_sum6")
 
 
 def jacobi_copy_planes(dst_ptr, src_ptr, plane_elems, elem_bytes, nplanes, stream):

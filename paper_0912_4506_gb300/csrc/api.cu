@@ -46,6 +46,10 @@ int check_grid_args(int nx, int ny, int nz, int dtype, long long pitch) {
     return JAC_OK;
 }
 
+// Integer-pipe additions of a kernel variant in half additions per update (codes
+// of 16 and above select the unpacked accumulator with (code - 16) mod 8 additions).
+int emu_half_adds(int code) { return code >= 16 ? 2 * ((code - 16) & 7) : code; }
+
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
 // Run nsweeps of `mode` as a sequence of passes.  kernel: JAC_KERNEL_*.
@@ -70,7 +74,7 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         if (info_only) {
             std::memset(info_only, 0, sizeof(*info_only));
             info_only->kernel = JAC_KERNEL_PLAIN;
-            info_only->emu_adds = pe->nemu;
+            info_only->emu_adds = emu_half_adds(pe->nemu);
             info_only->t = 1;
             info_only->passes = nsweeps;
             info_only->tile_x = 32 * pe->V;
@@ -128,7 +132,7 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
             info_only->grid_x = gm.ntx;
             info_only->grid_y = gm.nty;
             info_only->grid_z = gm.nchunk;
-            info_only->emu_adds = e->emu;
+            info_only->emu_adds = emu_half_adds(e->emu);
         }
         return JAC_OK;
     }

@@ -4,6 +4,7 @@
 
 #include "../../include/jacobi.h"
 #include "emu.cuh"
+#include "emusum.cuh"
 #include "launch.h"
 
 namespace jac {
@@ -99,6 +100,42 @@ __global__ void emulated_add_kernel(const double* __restrict__ a, const double* 
         const bool ok = (X >> 52) >= 1 && (X >> 52) <= 2045 && (Y >> 52) >= 1 &&
                         (Y >> 52) <= 2045;
         out[i] = ok ? add_pos_exact(x, y) : __dadd_rn(x, y);
+    }
+}
+
+// Six-term sums through the exact accumulator (verification entry point of
+// emusum.cuh): out[i] = ((((x0 + x1) + x2) + x3) + x4) + x5 with x_j =
+// x[j * n + i], the additions done as the FP64 sweeps do them (all five through
+// the accumulator; a warp with a lane outside its window, or with an operand
+// that is not a positive normal double, on the FP64 unit).
+__global__ void emulated_sum6_kernel(const double* __restrict__ x, double* __restrict__ out,
+                                     long long n, uint32_t one) {
+    const unsigned FULL = 0xffffffffu;
+    const emusum::Mul km = emusum::make_mul(one);
+    for (long long base = (long long)blockIdx.x * blockDim.x; base < n;
+         base += (long long)gridDim.x * blockDim.x) {
+        const long long i = base + threadIdx.x;
+        const bool live = i < n;
+        double v[6];
+        bool normal = true;
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            v[j] = live ? x[j * n + i] : 1.0;
+            const unsigned long long b = (unsigned long long)__double_as_longlong(v[j]);
+            normal = normal && (b >> 52) >= 1 && (b >> 52) <= 2045;
+        }
+        emusum::Words a = emusum::first_w(emusum::unpack_w(v[0], km), emusum::unpack_w(v[1], km), km);
+#pragma unroll
+        for (int j = 2; j < 6; ++j) emusum::add_w(a, emusum::unpack_w(v[j], km), km);
+        double s;
+        if (__any_sync(FULL, a.bad != 0u || !normal)) {
+            s = __dadd_rn(v[0], v[1]);
+#pragma unroll
+            for (int j = 2; j < 6; ++j) s = __dadd_rn(s, v[j]);
+        } else {
+            s = emusum::pack_w(a, km);
+        }
+        if (live) out[i] = s;
     }
 }
 
@@ -236,5 +273,14 @@ extern "C" int jacobi_emulated_add(const double* a, const double* b, double* out
     const long long blocks = std::min<long long>((n + 255) / 256, 4096);
     jac::emulated_add_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
         a, b, out, n);
+    return cudaGetLastError() == cudaSuccess ? JAC_OK : JAC_ECUDA;
+}
+
+extern "C" int jacobi_emulated_sum6(const double* x, double* out, long long n, void* stream) {
+    if (n < 0 || (n > 0 && (!x || !out))) return JAC_EINVAL;
+    if (n == 0) return JAC_OK;
+    const long long blocks = std::min<long long>((n + 255) / 256, 4096);
+    jac::emulated_sum6_kernel<<<(unsigned)blocks, 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        x, out, n, 1u);
     return cudaGetLastError() == cudaSuccess ? JAC_OK : JAC_ECUDA;
 }

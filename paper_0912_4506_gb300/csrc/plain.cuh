@@ -12,6 +12,7 @@
 
 #include "common.cuh"
 #include "emu.cuh"
+#include "emusum.cuh"
 
 namespace jac {
 
@@ -180,6 +181,92 @@ __device__ __forceinline__ void plain_march_shallow(const typename Tr::S* __rest
     (void)loadable;
 }
 
+// NEMU >= kAccBase (FP64): NEMU = kAccBase + K + 8 F; the first K of the five additions of
+// every update run through the unpacked exact accumulator of emusum.cuh; a warp
+// with a lane whose exponent gaps leave that routine's window recomputes those
+// additions on the FP64 unit.  The other additions and the product stay on the
+// FP64 unit.  F selects the form of the word arithmetic (emusum.cuh).
+constexpr int kAccBase = 16;
+
+template <class Tr, int V, int K, int F>
+__device__ __forceinline__ void plain_march_acc(const double* __restrict__ A,
+                                                double* __restrict__ B, const Geom& g, int k0,
+                                                int k1, int x0, int lane,
+                                                const bool (&interior)[V], bool left_ok,
+                                                bool right_ok, long long row, uint32_t one) {
+    static_assert(K >= 1 && K <= 5, "1..5 additions on the integer pipes");
+    const emusum::Mul km = emusum::make_mul(one);
+    const unsigned FULL = 0xffffffffu;
+    const double c6 = Tr::sixth();
+    bool okl[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) okl[e] = (x0 + e) < g.px;
+    auto load = [&](const double* p, double (&out)[V]) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) out[e] = okl[e] ? __ldg(p + e) : 0.0;
+    };
+    const long long plane = g.plane, px = g.px;
+    const double* pa = A + row + plane * k0;
+    double* pb = B + row + plane * k0;
+    double dn[V], ct[V], up[V], no[V], so[V];
+    load(pa - plane, dn);
+    load(pa, ct);
+#pragma unroll 1
+    for (int k = k0; k <= k1; ++k) {
+        load(pa + plane, up);
+        load(pa - px, no);
+        load(pa + px, so);
+        double left = __shfl_up_sync(FULL, ct[V - 1], 1);
+        double right = __shfl_down_sync(FULL, ct[0], 1);
+        if (lane == 0) left = left_ok ? __ldg(pa - 1) : 0.0;
+        if (lane == 31) right = right_ok ? __ldg(pa + V) : 0.0;
+        double x[V][6];
+        emusum::Words acc[V];
+        uint32_t bad = 0;
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            x[e][0] = (e == 0) ? left : ct[e - 1];
+            x[e][1] = (e == V - 1) ? right : ct[e + 1];
+            x[e][2] = no[e];
+            x[e][3] = so[e];
+            x[e][4] = dn[e];
+            x[e][5] = up[e];
+            acc[e] = emusum::first_w<F>(emusum::unpack_w(x[e][0], km),
+                                        emusum::unpack_w(x[e][1], km), km);
+#pragma unroll
+            for (int i = 2; i <= K; ++i)
+                emusum::add_w<F>(acc[e], emusum::unpack_w(x[e][i], km), km);
+            // cells outside the interior are never stored: their gaps do not count
+            if (interior[e]) bad |= acc[e].bad;
+        }
+        double s[V];
+        if (__any_sync(FULL, bad != 0u)) {
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                s[e] = __dadd_rn(x[e][0], x[e][1]);
+#pragma unroll
+                for (int i = 2; i <= K; ++i) s[e] = __dadd_rn(s[e], x[e][i]);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e) s[e] = emusum::pack_w(acc[e], km);
+        }
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+#pragma unroll
+            for (int i = K + 1; i <= 5; ++i) s[e] = __dadd_rn(s[e], x[e][i]);
+            if (interior[e]) pb[e] = __dmul_rn(s[e], c6);
+        }
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            dn[e] = ct[e];
+            ct[e] = up[e];
+        }
+        pa += plane;
+        pb += plane;
+    }
+}
+
 // `fast` (FP64, NEMU > 0): device flag written by range_check_kernel; when it is
 // set every value of A lies in [2^-1000, 2^1000], and by the maximum principle of
 // the averaging sweep so does every later value, so the emulated additions are
@@ -215,7 +302,14 @@ __global__ void __launch_bounds__(32 * WY)
     const bool right_ok = (x0 + V) < g.px;
     const long long row = g.lin(x0 < g.px ? x0 : 0, y, 0);
 
-    if constexpr (sizeof(typename Tr::S) == 8) {
+    if constexpr (sizeof(typename Tr::S) == 8 && NEMU >= kAccBase) {
+        if (fast != nullptr && *fast)
+            plain_march_acc<Tr, V, ((NEMU - kAccBase) & 7), ((NEMU - kAccBase) / 8)>(
+                A, B, g, k0, k1, x0, lane, interior, left_ok, right_ok, row, one);
+        else
+            plain_march_shallow<Tr, V, 0>(A, B, g, k0, k1, x0, y, lane, loadable, interior,
+                                          all_interior, left_ok, right_ok, row, one);
+    } else if constexpr (sizeof(typename Tr::S) == 8) {
         if (NEMU > 0 && fast != nullptr && *fast)
             plain_march_shallow<Tr, V, NEMU>(A, B, g, k0, k1, x0, y, lane, loadable, interior,
                                              all_interior, left_ok, right_ok, row, one);

@@ -17,8 +17,10 @@ constexpr int kModes = 3;      // MODE_PLAIN, MODE_RHS, MODE_ADJ
 constexpr int kCacheSlots = 64;
 
 // Integer-pipe additions of the FP64 plain sweep when the range check allows
-// them, in half additions per plane (3 of 5 additions); JACOBI_F64_EMU overrides.
-constexpr int kDefaultF64Emu = 6;
+// them: 44 = 4 of the 5 additions through the unpacked accumulator, word form 3
+// (the fastest measured, see tb_f64.cu); JACOBI_F64_EMU selects another entry
+// (0: all on the FP64 unit, 6: per-addition routine, 16 + K + 8F: accumulator).
+constexpr int kDefaultF64Emu = 44;
 
 std::mutex g_mu;
 
@@ -193,7 +195,7 @@ const PlainEntry* plain_for(int dtype) {
             want = kDefaultF64Emu;
             if (const char* e = getenv("JACOBI_F64_EMU")) {
                 const int v = atoi(e);
-                if (v >= 0 && v <= 8) want = v;
+                if (v >= 0 && v <= 47) want = v;
             }
         });
         int n = 0;

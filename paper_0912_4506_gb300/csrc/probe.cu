@@ -10,6 +10,7 @@
 
 #include "../../include/jacobi.h"
 #include "emu.cuh"
+#include "emusum.cuh"
 
 namespace jac {
 
@@ -75,6 +76,26 @@ __global__ void __launch_bounds__(256) pipe_probe_kernel(double* out, int iters,
             for (int c = 0; c < kChains; ++c) x[c] = mad_lo(x[c], y, z + c);
 #pragma unroll
         for (int c = 0; c < kChains; ++c) acc += (double)x[c];
+    } else if constexpr (KIND == JAC_PROBE_ACC_ADD) {
+        // the FP64 sweeps' unpacked running sum: additions of an operand whose
+        // exponent is at most 9 below the sum's (reset into [1, 2) every 64)
+        const emusum::Mul km = emusum::make_mul(seed);
+        emusum::Words a[kChains];
+        const emusum::UnpW y = emusum::unpack_w(0.75 + (double)(seed & 7) * 0x1p-40, km);
+#pragma unroll
+        for (int c = 0; c < kChains; ++c)
+            a[c] = emusum::first_w(emusum::unpack_w(1.0 + (double)(tid + c) * 0x1p-30, km), y, km);
+#pragma unroll 1
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int c = 0; c < kChains; ++c) emusum::add_w(a[c], y, km);
+            if ((i & 63) == 63) {
+#pragma unroll
+                for (int c = 0; c < kChains; ++c) a[c].e = 1023u;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) acc += emusum::pack_w(a[c], km) + (double)a[c].bad;
     } else {  // JAC_PROBE_EMU_ADD: the sweep's exact binary64 addition on integer pipes
         double x[kChains];
         // operands of similar magnitude, as in a sweep: the running sum doubles
@@ -120,6 +141,10 @@ extern "C" int jacobi_pipe_probe(int kind, double* out, int blocks, int threads,
             break;
         case JAC_PROBE_IMAD:
             jac::pipe_probe_kernel<JAC_PROBE_IMAD><<<blocks, threads, 0, st>>>(out, iters, seed);
+            break;
+        case JAC_PROBE_ACC_ADD:
+            jac::pipe_probe_kernel<JAC_PROBE_ACC_ADD><<<blocks, threads, 0, st>>>(out, iters,
+                                                                                   seed);
             break;
         case JAC_PROBE_EMU_ADD:
             jac::pipe_probe_kernel<JAC_PROBE_EMU_ADD><<<blocks, threads, 0, st>>>(out, iters,

@@ -43,12 +43,14 @@
 
 #include "common.cuh"
 #include "emu.cuh"
+#include "emusum.cuh"
 
 namespace jac {
 
 enum { MODE_PLAIN = 0, MODE_RHS = 1, MODE_ADJ = 2 };
 
 constexpr int kRing = 6;  // TMA ring slots (the unroll period)
+constexpr int kAccBaseTB = 16;  // EMU >= this: accumulator with EMU - 16 additions
 
 struct TBArgs {
     Geom g;
@@ -224,10 +226,14 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
         }
     };
 
+    // EMU >= kAccBaseTB (FP64 plain sweeps): the first EMU - kAccBaseTB additions
+    // of every update through the exact accumulator of emusum.cuh instead
+    constexpr bool kAcc = EMU >= kAccBaseTB && std::is_same<C, double>::value &&
+                          MODE == MODE_PLAIN;
     // addition number idx (0..4) of an update: the first EMU on the integer pipes
     const uint32_t one = a.one;
     auto add = [one](int idx, C x, C y) -> C {
-        if constexpr (EMU > 0 && std::is_same<C, double>::value) {
+        if constexpr (EMU > 0 && EMU < kAccBaseTB && std::is_same<C, double>::value) {
             if (idx < EMU) return add_pos_exact_f(x, y, one);
         }
         return Tr::add(x, y);
@@ -278,6 +284,48 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
             C out[V];
             if (zin) {
                 C val[V];
+                if constexpr (kAcc) {
+                    // the first K additions through the exact accumulator; a warp
+                    // with an interior lane outside its window redoes them on the
+                    // FP64 unit (lanes off the interior keep their old values)
+                    constexpr int K = EMU - kAccBaseTB;
+                    C x[V][6];
+                    emusum::Acc acc[V];
+                    uint32_t bad = 0;
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+                        x[e][0] = (e == 0) ? left : r[s - 1][CUR][e - 1];
+                        x[e][1] = (e == V - 1) ? right : r[s - 1][CUR][e + 1];
+                        x[e][2] = Tr::ld(vn.v[e]);
+                        x[e][3] = Tr::ld(vs.v[e]);
+                        x[e][4] = r[s - 1][OLD][e];
+                        x[e][5] = r[s - 1][NEW][e];
+                        // the 64-bit form: fewer registers than the word form here,
+                        // and faster at every depth measured
+                        acc[e] = emusum::first(emusum::unpack(x[e][0]), emusum::unpack(x[e][1]));
+#pragma unroll
+                        for (int i = 2; i <= K; ++i) emusum::add(acc[e], emusum::unpack(x[e][i]));
+                        if (FAST || inxy[e]) bad |= acc[e].bad;
+                    }
+                    C sum[V];
+                    if (__any_sync(FULL, bad != 0u)) {
+#pragma unroll
+                        for (int e = 0; e < V; ++e) {
+                            sum[e] = Tr::add(x[e][0], x[e][1]);
+#pragma unroll
+                            for (int i = 2; i <= K; ++i) sum[e] = Tr::add(sum[e], x[e][i]);
+                        }
+                    } else {
+#pragma unroll
+                        for (int e = 0; e < V; ++e) sum[e] = emusum::pack(acc[e]);
+                    }
+#pragma unroll
+                    for (int e = 0; e < V; ++e) {
+#pragma unroll
+                        for (int i = K + 1; i <= 5; ++i) sum[e] = Tr::add(sum[e], x[e][i]);
+                        val[e] = Tr::mul(sum[e], c6);
+                    }
+                } else {
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
                     const C l = (e == 0) ? left : r[s - 1][CUR][e - 1];
@@ -289,6 +337,7 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
                     sum = add(4, sum, r[s - 1][NEW][e]);
                     if (MODE == MODE_RHS) sum = Tr::add(sum, Tr::ld(vr.v[e]));
                     val[e] = Tr::mul(sum, c6);
+                }
                 }
                 // round to storage precision (plain bf16 sweeps of depth >= 2: two
                 // values per conversion; the one-value form measured faster at depth

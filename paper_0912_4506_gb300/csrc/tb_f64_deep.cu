@@ -7,8 +7,8 @@
 namespace jac {
 
 static const TBEntry kTB[] = {
-    JAC_TBE(F64, 1, 32, 5, MODE_PLAIN, 6, 3), JAC_TBE(F64, 1, 32, 6, MODE_PLAIN, 6, 3),
-    JAC_TBE(F64, 1, 24, 7, MODE_PLAIN, 6, 3), JAC_TBE(F64, 1, 24, 8, MODE_PLAIN, 6, 3),
+    JAC_TBE(F64, 1, 32, 5, MODE_PLAIN, 6, 20), JAC_TBE(F64, 1, 32, 6, MODE_PLAIN, 6, 20),
+    JAC_TBE(F64, 1, 24, 7, MODE_PLAIN, 6, 20), JAC_TBE(F64, 1, 24, 8, MODE_PLAIN, 6, 20),
 };
 JAC_TABLE(tb_entries_f64_deep, kTB)
 

@@ -48,7 +48,7 @@ int check_grid_args(int nx, int ny, int nz, int dtype, long long pitch) {
 
 // Integer-pipe additions of a kernel variant in half additions per update (codes
 // of 16 and above select the unpacked accumulator with (code - 16) mod 8 additions).
-int emu_half_adds(int code) { return code >= 16 ? 2 * ((code - 16) & 7) : code; }
+int emu_half_adds(int code) { return code >= 16 ? 2 * ((code - 16) & 7) : code; }  // K bits
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 

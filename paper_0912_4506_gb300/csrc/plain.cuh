@@ -272,10 +272,10 @@ __device__ __forceinline__ void plain_march_acc(const double* __restrict__ A,
 // the averaging sweep so does every later value, so the emulated additions are
 // valid for the whole call.
 template <class Tr, int V, int WY, int NEMU>
-__global__ void __launch_bounds__(32 * WY)
-    plain_sweep_kernel(const typename Tr::S* __restrict__ A, typename Tr::S* __restrict__ B,
-                       const Geom g, const int kchunk, const int* __restrict__ fast,
-                       const uint32_t one) {
+__device__ __forceinline__ void plain_sweep_body(const typename Tr::S* __restrict__ A,
+                                                 typename Tr::S* __restrict__ B, const Geom& g,
+                                                 const int kchunk, const int* __restrict__ fast,
+                                                 const uint32_t one) {
     // FP64 and V == 1: interior-aligned cells (scalar loads); else 16-byte vectors
     constexpr int XOFF = (V == 1 || sizeof(typename Tr::S) == 8) ? 1 : 0;
     const int lane = threadIdx.x;
@@ -304,7 +304,7 @@ __global__ void __launch_bounds__(32 * WY)
 
     if constexpr (sizeof(typename Tr::S) == 8 && NEMU >= kAccBase) {
         if (fast != nullptr && *fast)
-            plain_march_acc<Tr, V, ((NEMU - kAccBase) & 7), ((NEMU - kAccBase) / 8)>(
+            plain_march_acc<Tr, V, ((NEMU - kAccBase) & 7), (((NEMU - kAccBase) / 8) & 3)>(
                 A, B, g, k0, k1, x0, lane, interior, left_ok, right_ok, row, one);
         else
             plain_march_shallow<Tr, V, 0>(A, B, g, k0, k1, x0, y, lane, loadable, interior,
@@ -320,6 +320,25 @@ __global__ void __launch_bounds__(32 * WY)
         plain_march<Tr, V>(A, B, g, k0, k1, lane, loadable, interior, all_interior, left_ok,
                            right_ok, row);
     }
+}
+
+template <class Tr, int V, int WY, int NEMU>
+__global__ void __launch_bounds__(32 * WY)
+    plain_sweep_kernel(const typename Tr::S* __restrict__ A, typename Tr::S* __restrict__ B,
+                       const Geom g, const int kchunk, const int* __restrict__ fast,
+                       const uint32_t one) {
+    plain_sweep_body<Tr, V, WY, NEMU>(A, B, g, kchunk, fast, one);
+}
+
+// The same sweep compiled for at least 1280 resident threads per SM (so at most
+// 51 registers a thread): variant codes 48 and above, whose register demand
+// otherwise costs resident warps (the accumulator forms).
+template <class Tr, int V, int WY, int NEMU>
+__global__ void __launch_bounds__(32 * WY, (1280 / (32 * WY) > 0 ? 1280 / (32 * WY) : 1))
+    plain_sweep_kernel_capped(const typename Tr::S* __restrict__ A,
+                              typename Tr::S* __restrict__ B, const Geom g, const int kchunk,
+                              const int* __restrict__ fast, const uint32_t one) {
+    plain_sweep_body<Tr, V, WY, NEMU>(A, B, g, kchunk, fast, one);
 }
 
 }  // namespace jac

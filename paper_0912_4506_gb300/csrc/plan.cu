@@ -17,10 +17,11 @@ constexpr int kModes = 3;      // MODE_PLAIN, MODE_RHS, MODE_ADJ
 constexpr int kCacheSlots = 64;
 
 // Integer-pipe additions of the FP64 plain sweep when the range check allows
-// them: 44 = 4 of the 5 additions through the unpacked accumulator, word form 3
-// (the fastest measured, see tb_f64.cu); JACOBI_F64_EMU selects another entry
-// (0: all on the FP64 unit, 6: per-addition routine, 16 + K + 8F: accumulator).
-constexpr int kDefaultF64Emu = 44;
+// them: 76 = 4 of the 5 additions through the unpacked accumulator, word form 3,
+// register-capped kernel (the fastest measured, see tb_f64.cu); JACOBI_F64_EMU
+// selects another entry (0: all on the FP64 unit, 6: per-addition routine,
+// 16 + K + 8F: accumulator, +32: register-capped kernel).
+constexpr int kDefaultF64Emu = 76;
 
 std::mutex g_mu;
 
@@ -195,7 +196,7 @@ const PlainEntry* plain_for(int dtype) {
             want = kDefaultF64Emu;
             if (const char* e = getenv("JACOBI_F64_EMU")) {
                 const int v = atoi(e);
-                if (v >= 0 && v <= 47) want = v;
+                if (v >= 0 && v <= 79) want = v;
             }
         });
         int n = 0;

@@ -15,12 +15,15 @@ JAC_TABLE(tb_entries_f64, kTB)
 
 // plain sweeps: entry 0 keeps every addition on the FP64 unit; 6 does 3 of the
 // 5 additions one at a time on the integer pipes (emu.cuh); 16 + K + 8F sends the
-// first K additions through the unpacked accumulator (emusum.cuh) in word form F.
-// 44 (K = 4, F = 3) measured fastest at 512^3 on GB300: 201 GLUP/s, against 197
-// for F = 0, 167 / 156 with K = 3 / 5, 166 for entry 6 and 85 for entry 0.
+// first K additions through the unpacked accumulator (emusum.cuh) in word form F,
+// and + 32 compiles it for 5 resident CTAs per SM (at most 51 registers).  76
+// (K = 4, F = 3, capped) measured fastest at 512^3 on GB300: 201 GLUP/s, against
+// 193 for F = 0 capped, 197 for F = 0, 167 / 156 with K = 3 / 5, 166 for entry 6
+// and 85 for entry 0.
 static const PlainEntry kPlain[] = {JAC_PLAIN(F64, 2, 8, 0),  JAC_PLAIN(F64, 2, 8, 6),
                                     JAC_PLAIN(F64, 2, 8, 19), JAC_PLAIN(F64, 2, 8, 20),
-                                    JAC_PLAIN(F64, 2, 8, 21), JAC_PLAIN(F64, 2, 8, 44)};
+                                    JAC_PLAIN(F64, 2, 8, 21), JAC_PLAIN(F64, 2, 8, 44),
+                                    JAC_PLAIN(F64, 2, 8, 52), JAC_PLAIN(F64, 2, 8, 76)};
 const PlainEntry* plain_entries_f64(int* n) {
     *n = (int)(sizeof(kPlain) / sizeof(kPlain[0]));
     return kPlain;

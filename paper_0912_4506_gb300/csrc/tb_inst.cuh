@@ -24,9 +24,21 @@ template <class TR, int V, int WY, int NEMU>
 cudaError_t plain_launch(const void* A, void* B, const Geom& g, int kchunk, dim3 grid,
                          const int* fast, cudaStream_t st) {
     using S = typename TR::S;
-    plain_sweep_kernel<TR, V, WY, NEMU><<<grid, dim3(32, WY), 0, st>>>(
-        static_cast<const S*>(A), static_cast<S*>(B), g, kchunk, fast, 1u);
+    if constexpr (NEMU >= 48)
+        plain_sweep_kernel_capped<TR, V, WY, NEMU><<<grid, dim3(32, WY), 0, st>>>(
+            static_cast<const S*>(A), static_cast<S*>(B), g, kchunk, fast, 1u);
+    else
+        plain_sweep_kernel<TR, V, WY, NEMU><<<grid, dim3(32, WY), 0, st>>>(
+            static_cast<const S*>(A), static_cast<S*>(B), g, kchunk, fast, 1u);
     return cudaGetLastError();
+}
+
+template <class TR, int V, int WY, int NEMU>
+const void* plain_kernel_ptr() {
+    if constexpr (NEMU >= 48)
+        return reinterpret_cast<const void*>(&plain_sweep_kernel_capped<TR, V, WY, NEMU>);
+    else
+        return reinterpret_cast<const void*>(&plain_sweep_kernel<TR, V, WY, NEMU>);
 }
 
 }  // namespace jac
@@ -40,7 +52,7 @@ cudaError_t plain_launch(const void* A, void* B, const Geom& g, int kchunk, dim3
 
 #define JAC_PLAIN(TR, V, WY, NEMU) \
     {TR::kDtype, V, WY, NEMU, &::jac::plain_launch<TR, V, WY, NEMU>, \
-     reinterpret_cast<const void*>(&::jac::plain_sweep_kernel<TR, V, WY, NEMU>)}
+     ::jac::plain_kernel_ptr<TR, V, WY, NEMU>()}
 
 #define JAC_TABLE(NAME, ARR)                                  \
     const TBEntry* NAME(int* n) {                             \

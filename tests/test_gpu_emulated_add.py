@@ -190,7 +190,7 @@ def test_blocked_fp64_zero_and_negative_values_use_fp64_unit():
         assert np.array_equal(got, oracle.sweeps(u0, 9, nx=nx)[:, :, :nx + 2]), t
 
 
-@pytest.mark.parametrize("nemu", [0, 6, 19, 20, 21, 44])
+@pytest.mark.parametrize("nemu", [0, 6, 19, 20, 21, 44, 52, 76])
 def test_every_emulation_split_bit_exact(nemu, monkeypatch):
     """Run each split in a fresh process (the split is read once per process)."""
     import subprocess

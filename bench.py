@@ -388,7 +388,7 @@ def variant_batched(dev):
             "depth_histogram": hist, "launches_per_run": 1}
 
 
-def variant_adjoint(dev, n=256, nsweeps=50, t_fwd=3, t_adj=(("f32", 4), ("f64", 1))):
+def variant_adjoint(dev, n=256, nsweeps=50, t_fwd=3, t_adj=(("f32", 3), ("f64", 1))):
     """256^3 FP32, 50 sweeps: forward (blocked), adjoint (blocked, with the boundary
     gradient), beside the plain FP32 sweep; error of the FP32 gradient against the
     FP64 adjoint of the same loss.  Depths: the fastest measured on GB300 for each

@@ -170,15 +170,20 @@ JAC_API int jacobi_residual_accumulate(int nx, int ny, int nz, const double *u_i
 
 /*
  * jacobi_adjoint — reverse sweeps for the gradient of L = sum(W * A_n) (A_n the
- * result of n forward sweeps).  The handle's grids hold the adjoint field:
- * A = lambda_n (W on the interior, zero boundary layer) on entry.  Each sweep
- * applies the transpose of one forward sweep, which is the same stencil on a
- * zero boundary, and adds RN(1/6) * lambda_s at the interior neighbour of every
- * face cell of the boundary layer into grad_bdry (a grid of the handle's
- * layout and dtype; only face cells are touched, in sweep order, one thread per
- * cell: deterministic).  After nsweeps the interior of the final grid is dL/dA_0
- * and grad_bdry (pre-set by the caller to W on the boundary layer) is dL/dg.
- * dtype JAC_F32 or JAC_F64.
+ * result of n forward sweeps of Eq. 1).  The handle's grids hold the adjoint
+ * field: A = lambda_n (W on the interior, zero boundary layer) on entry.  Each
+ * sweep applies the transpose of one forward sweep, which is the same stencil on
+ * a zero boundary, and every face cell b of the boundary layer receives
+ * RN(1/6) * lambda_s at its interior neighbour: the blocked kernel stores those
+ * values per sweep in a face buffer the handle owns (2*(ny*nz + nx*nz + nx*ny)
+ * elements per sweep, allocated on the first call that needs more and kept until
+ * jacobi_destroy; JAC_ENOMEM if that allocation fails), and one kernel at the end
+ * of the call adds them into grad_bdry in sweep order (lambda_n's share first),
+ * so the result is deterministic.  grad_bdry: a grid of the handle's layout and
+ * dtype, pre-set by the caller (the direct term W on the boundary layer); only its
+ * face cells are written.  After nsweeps the interior of the final grid is
+ * dL/dA_0 and grad_bdry is dL/dg.  t as in jacobi_sweep (t = 0: depth 3 for
+ * FP32, 1 for FP64; deepest 4).  dtype JAC_F32 or JAC_F64.
  */
 JAC_API int jacobi_adjoint(jacobi_t h, void *grad_bdry, int nsweeps, int t,
                    int *final_is_b);

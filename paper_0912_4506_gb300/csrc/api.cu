@@ -33,6 +33,8 @@ struct jacobi_s {
     CUtensorMap map_rho;  // right-hand side of the correction sweeps (last rho seen)
     const void* rho_ptr;
     int rho_box_x, rho_box_y;
+    void* fbuf;           // adjoint: face values per sweep (owned, grown on demand)
+    size_t fbuf_bytes;
 };
 
 namespace {
@@ -155,7 +157,29 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         }
     }
 
+    // adjoint: one row of face values per sweep, added to the gradient at the end
+    const long long fstride = 2LL * ((long long)h->g.ny * h->g.nz +
+                                     (long long)h->g.nx * h->g.nz +
+                                     (long long)h->g.nx * h->g.ny);
+    if (mode == MODE_ADJ && nsweeps > 0) {
+        const size_t need = (size_t)fstride * (size_t)nsweeps * (size_t)elem_size(h->dtype);
+        if (need > h->fbuf_bytes) {
+            if (h->fbuf) {
+                if (cudaStreamSynchronize(h->stream) != cudaSuccess) return JAC_ECUDA;
+                cudaFree(h->fbuf);
+                h->fbuf = nullptr;
+                h->fbuf_bytes = 0;
+            }
+            if (cudaMalloc(&h->fbuf, need) != cudaSuccess) {
+                h->fbuf = nullptr;
+                return JAC_ENOMEM;
+            }
+            h->fbuf_bytes = need;
+        }
+    }
+
     int cur_b = 0;  // 0: current data in A
+    int sweep0 = 0;
     for (int p = 0; p < dp.passes(); ++p) {
         const TBEntry* e = tb_entry(h->dtype, mode, dp.depth(p));
         if (!e) return JAC_EUNSUPPORTED;
@@ -174,6 +198,9 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         args.g = h->g;
         args.dst = cur_b ? h->a : h->b;
         args.grad = grad;
+        args.fbuf = h->fbuf;
+        args.fstride = fstride;
+        args.sweep0 = sweep0;
         args.ox = gm.ox;
         args.x0_first = gm.x0_first;
         args.kz = gm.kz;
@@ -193,7 +220,12 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
             cudaSuccess)
             return JAC_ECUDA;
         cur_b ^= 1;
+        sweep0 += e->T;
     }
+    if (mode == MODE_ADJ && nsweeps > 0 &&
+        launch_face_reduce(h->dtype, grad, h->g, h->fbuf, fstride, nsweeps, h->stream) !=
+            cudaSuccess)
+        return JAC_ECUDA;
     if (final_is_b) *final_is_b = cur_b;
     return JAC_OK;
 }
@@ -343,6 +375,7 @@ int jacobi_destroy(jacobi_t h) {
     cudaSetDevice(h->device);
     cudaStreamSynchronize(h->stream);
     cudaFree(h->status);
+    if (h->fbuf) cudaFree(h->fbuf);
     delete h;
     return JAC_OK;
 }

@@ -103,6 +103,54 @@ __global__ void emulated_add_kernel(const double* __restrict__ a, const double* 
     }
 }
 
+// Boundary gradient of the adjoint sweeps: grad[b] += c * lambda_s[m_b] for every
+// face cell b (interior neighbour m_b) and sweep s, added in sweep order (the
+// reverse-mode order: the last forward sweep first) from the face buffer the
+// blocked adjoint kernel fills.  One thread per face cell; the face buffer holds
+// nsweeps rows of fstride values (x faces, y faces, z faces, low face first).
+template <class S>
+__global__ void face_reduce_kernel(S* __restrict__ grad, const Geom g,
+                                   const S* __restrict__ fbuf, long long fstride, int nsweeps) {
+    const long long fxs = (long long)g.ny * g.nz, fys = (long long)g.nx * g.nz;
+    const long long fzs = (long long)g.nx * g.ny;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < fstride;
+         i += (long long)gridDim.x * blockDim.x) {
+        int x, y, z;
+        if (i < 2 * fxs) {
+            const long long f = i / fxs, r = i % fxs;
+            z = (int)(r / g.ny) + 1;
+            y = (int)(r % g.ny) + 1;
+            x = f == 0 ? 0 : g.nx + 1;
+        } else if (i < 2 * fxs + 2 * fys) {
+            const long long f = (i - 2 * fxs) / fys, r = (i - 2 * fxs) % fys;
+            z = (int)(r / g.nx) + 1;
+            x = (int)(r % g.nx) + 1;
+            y = f == 0 ? 0 : g.ny + 1;
+        } else {
+            const long long f = (i - 2 * fxs - 2 * fys) / fzs, r = (i - 2 * fxs - 2 * fys) % fzs;
+            y = (int)(r / g.nx) + 1;
+            x = (int)(r % g.nx) + 1;
+            z = f == 0 ? 0 : g.nz + 1;
+        }
+        S acc = grad[g.lin(x, y, z)];
+        for (int s = 0; s < nsweeps; ++s) acc = acc + fbuf[(long long)s * fstride + i];
+        grad[g.lin(x, y, z)] = acc;
+    }
+}
+
+cudaError_t launch_face_reduce(int dtype, void* grad, const Geom& g, const void* fbuf,
+                               long long fstride, int nsweeps, cudaStream_t st) {
+    const int threads = 256;
+    const long long blocks = std::min<long long>((fstride + threads - 1) / threads, 8192);
+    if (dtype == 0)
+        face_reduce_kernel<double><<<(unsigned)blocks, threads, 0, st>>>(
+            static_cast<double*>(grad), g, static_cast<const double*>(fbuf), fstride, nsweeps);
+    else
+        face_reduce_kernel<float><<<(unsigned)blocks, threads, 0, st>>>(
+            static_cast<float*>(grad), g, static_cast<const float*>(fbuf), fstride, nsweeps);
+    return cudaGetLastError();
+}
+
 // Six-term sums through the exact accumulator (verification entry point of
 // emusum.cuh): out[i] = ((((x0 + x1) + x2) + x3) + x4) + x5 with x_j =
 // x[j * n + i], the additions done as the FP64 sweeps do them (all five through

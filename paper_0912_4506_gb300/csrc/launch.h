@@ -60,6 +60,8 @@ const PlainEntry* plain_entry_bf16();
 // Auxiliary kernels (aux.cu).
 cudaError_t launch_boundary_copy(int dtype, const void* A, void* B, const Geom& g,
                                  cudaStream_t st);
+cudaError_t launch_face_reduce(int dtype, void* grad, const Geom& g, const void* fbuf,
+                               long long fstride, int nsweeps, cudaStream_t st);
 cudaError_t launch_range_check(const double* A, const Geom& g, int* flag, cudaStream_t st);
 cudaError_t launch_residual(const double* u_in, double* u_out, const Geom& gu,
                             const void* e, void* rho, int lo_dtype, const Geom& glo,

@@ -2,6 +2,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdio>
 #include <cstdlib>
 #include <mutex>
 
@@ -37,10 +38,30 @@ const Tables& tables() {
         for (auto& d : t.e)
             for (auto& m : d)
                 for (auto& p : m) p = nullptr;
-        auto add = [](const TBEntry* p, int n) {
-            for (int i = 0; i < n; ++i)
-                if (p[i].T >= 1 && p[i].T <= kMaxDepth)
-                    t.e[p[i].dtype][p[i].mode][p[i].T] = &p[i];
+        // the first entry of a depth is its kernel; later ones are alternate tile
+        // shapes, chosen only through JACOBI_TB_SHAPE (measurement runs)
+        struct Want { int mode, T, V, NW; } want[16];
+        int nwant = 0;
+        if (const char* env = getenv("JACOBI_TB_SHAPE")) {
+            // "mode,T,V,NW;mode,T,V,NW;..."
+            const char* c = env;
+            while (*c && nwant < 16) {
+                Want w{};
+                if (sscanf(c, "%d,%d,%d,%d", &w.mode, &w.T, &w.V, &w.NW) == 4) want[nwant++] = w;
+                while (*c && *c != ';') ++c;
+                if (*c == ';') ++c;
+            }
+        }
+        auto add = [&](const TBEntry* p, int n) {
+            for (int i = 0; i < n; ++i) {
+                if (p[i].T < 1 || p[i].T > kMaxDepth) continue;
+                const TBEntry*& slot = t.e[p[i].dtype][p[i].mode][p[i].T];
+                if (!slot) slot = &p[i];
+                for (int k = 0; k < nwant; ++k)
+                    if (want[k].mode == p[i].mode && want[k].T == p[i].T && want[k].V == p[i].V &&
+                        want[k].NW == p[i].NW)
+                        slot = &p[i];
+            }
         };
         int n = 0;
         const TBEntry* p;
@@ -179,13 +200,13 @@ TileGeom tile_geom(int dtype, const Geom& g, int V, int NW, int T, long long slo
 // Measured fastest at 512^3 on GB300: FP64 is bound by its arithmetic pipes, so
 // blocking (which adds halo recompute) cannot help the plain FP64 sweep; plain
 // FP32/bf16 sweeps peak at depth 3 (128 x 32 tiles), FP32 correction sweeps at 4
-// (tied with 3), bf16 correction sweeps at 2, adjoint sweeps at 4 (FP32) and 1
+// (tied with 3), bf16 correction sweeps at 2, adjoint sweeps at 3 (FP32) and 1
 // (FP64).
 int default_t(int dtype, int mode) {
     if (dtype == JAC_F64) return 1;
     if (mode == MODE_PLAIN) return 3;
     if (mode == MODE_RHS) return dtype == JAC_BF16 ? 2 : 4;
-    return 4;
+    return 3;
 }
 
 const PlainEntry* plain_for(int dtype) {

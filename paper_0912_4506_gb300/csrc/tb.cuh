@@ -35,8 +35,9 @@
 //
 // Modes: MODE_PLAIN (Eq. 1), MODE_RHS (the refinement's correction sweep, adds
 // rho before the product; rho's planes arrive by TMA beside the grid's), MODE_ADJ
-// (the adjoint sweep on a zero boundary, and accumulation of RN(1/6)*lambda at
-// the face-neighbouring interior cells into the boundary gradient).
+// (the adjoint sweep on a zero boundary; RN(1/6)*lambda at the face-neighbouring
+// interior cells of every level goes to a face buffer, read from shared memory
+// after each step's barrier, outside the k-march).
 #pragma once
 
 #include <type_traits>
@@ -55,7 +56,10 @@ constexpr int kAccBaseTB = 16;  // EMU >= this: accumulator with EMU - 16 additi
 struct TBArgs {
     Geom g;
     void* dst;          // output grid of the pass (level T)
-    void* grad;         // MODE_ADJ: boundary gradient grid (same layout)
+    void* grad;         // unused (kept for the layout of the argument block)
+    void* fbuf;         // MODE_ADJ: face buffer, c * lambda at face-adjacent cells
+    long long fstride;  // MODE_ADJ: elements per sweep in fbuf (all six faces)
+    int sweep0;         // MODE_ADJ: sweep index of this pass's level 0 in fbuf
     int ox;             // output tile width (multiple of the TMA alignment)
     int x0_first;       // x origin of tile 0's extended tile (aligned, may be < 0)
     int kz;             // output k-planes per CTA
@@ -179,50 +183,68 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
 
     const C c6 = Tr::sixth();
     S* dst = static_cast<S*>(a.dst);
-    S* grad = static_cast<S*>(a.grad);
     const long long rowoff = (long long)gy * g.px + gx0;  // valid only when used
     const int mycol = w * EX + lane * V;
-    // boundary-gradient accumulation (MODE_ADJ): face flags per cell, 5 bits each
-    // (x = 1, x = nx, y = 1, y = ny, cell owned), precomputed; z faces are uniform
-    // per plane.  (Kept in this form -- a 32-bit mask, a const flag, a pointer
-    // argument -- because other forms of this code, dead in the other modes, made
-    // the plain and correction k-marches issue ~9 % more instructions.)
-    uint32_t fmask = 0;
-    if (MODE == MODE_ADJ) {
-#pragma unroll
-        for (int e = 0; e < V; ++e) {
-            const int x = gx0 + e;
-            if (outxy[e])
-                fmask |= ((x == 1) ? 1u : 0u) | ((x == g.nx) ? 2u : 0u) | ((gy == 1) ? 4u : 0u) |
-                         ((gy == g.ny) ? 8u : 0u) | 16u;  // 16: cell owned (z faces)
-            if (e + 1 < V) fmask <<= 5;
+    // boundary gradient (MODE_ADJ): the output tile's cells in x and y, and which
+    // faces of the interior it touches (x = 1, x = nx, y = 1, y = ny)
+    const int cx0 = max(ox0, 1), cx1 = min(ox0 + a.ox, g.nx + 1);
+    const int cy0 = max(oy0, 1), cy1 = min(oy0 + OY, g.ny + 1);
+    const int ncols = max(cx1 - cx0, 0), nrows = max(cy1 - cy0, 0);
+    const int nfx = (MODE == MODE_ADJ) ? (int)(cx0 == 1) + (int)(cx1 == g.nx + 1) : 0;
+    const int nfy = (MODE == MODE_ADJ) ? (int)(cy0 == 1) + (int)(cy1 == g.ny + 1) : 0;
+    const int nxy = nfx * nrows + nfy * ncols;  // face cells per plane and level
+    static_assert(MODE != MODE_ADJ || 2 * EX + 2 * EY <= NW * 32,
+                  "one x/y face cell per thread at most");
+    // Thread tid < nxy owns one x/y face cell of the output tile for the whole tile:
+    // its offset in a shared-memory plane, and its place in a face-buffer row
+    // (base at plane 1, stride per plane).
+    const long long fxs = (long long)g.ny * g.nz, fys = (long long)g.nx * g.nz;
+    int f_sm = -1, f_qs = 0, f_base = 0;  // a face row has < 2^31 cells
+    if (MODE == MODE_ADJ && tid < nxy) {
+        int x, y, f, r = tid;
+        if (r < nfx * nrows) {
+            const int lo = (cx0 == 1) ? 1 : 0;  // which x faces the tile has
+            f = (lo && r >= nrows) ? 1 : (lo ? 0 : 1);
+            x = f == 0 ? 1 : g.nx;
+            y = cy0 + (r >= nrows ? r - nrows : r);
+            f_base = (int)(f * fxs) + (y - 1) - g.ny;  // plane q adds q * ny
+            f_qs = g.ny;
+        } else {
+            r -= nfx * nrows;
+            const int lo = (cy0 == 1) ? 1 : 0;
+            f = 2 + ((lo && r >= ncols) ? 1 : (lo ? 0 : 1));
+            y = f == 2 ? 1 : g.ny;
+            x = cx0 + (r >= ncols ? r - ncols : r);
+            f_base = (int)(2 * fxs + (f - 2) * fys) + (x - 1) - g.nx;  // plane q adds q * nx
+            f_qs = g.nx;
         }
+        f_sm = (y - Y0) * EX + (x - X0);
     }
-    constexpr uint32_t kXYFaces = 0x1EF7BDEFu & ((V >= 6) ? 0xFFFFFFFFu : ((1u << (5 * V)) - 1u));
-    const bool xy_face = (fmask & kXYFaces) != 0u;  // this thread owns an x or y face cell
-    auto adj_acc = [&](const C* v, int p) {
-        if constexpr (MODE != MODE_ADJ || !std::is_same<S, C>::value) return;
-        const bool zlo = p == 1, zhi = p == g.nz;
-        // tiles inside the interior in x and y own no x/y face: only the z faces
-        if (FAST ? !(zlo || zhi) : (!xy_face && !(zlo || zhi))) return;
-        if (p < kz0 || p >= kz1 || fmask == 0u) return;
-        C* gacc = reinterpret_cast<C*>(grad);  // the adjoint runs on FP32/FP64 grids
+    // After the barrier of a step, the planes every level produced in it are in
+    // shared memory: level 0 in the ring slot, level s in its level buffer.  For
+    // each level s < T whose plane q is one of this CTA's planes, the face-adjacent
+    // cells of the output tile give c * lambda to the face buffer (one store per
+    // cell and sweep, no atomics); a separate kernel adds them to the gradient in
+    // sweep order.
+    auto adj_faces = [&](const S* plane_s, int s, int q) {
+        if constexpr (MODE == MODE_ADJ) {
+            if (q < kz0 || q >= kz1) return;
+            S* fb = static_cast<S*>(a.fbuf) + (long long)(a.sweep0 + s) * a.fstride;
+            if (f_sm >= 0)
+                fb[f_base + q * f_qs] = Tr::st(Tr::mul(c6, Tr::ld(plane_s[f_sm])));
+            // z faces: plane 1 feeds face z = 0, plane nz face z = nz+1 (both if nz = 1);
+            // every thread stores its own output cells of the plane
+            if (q == 1 || q == g.nz) {
 #pragma unroll
-        for (int e = 0; e < V; ++e) {
-            const uint32_t f = (fmask >> (5 * (V - 1 - e))) & 31u;
-            if (!(f & 16u)) continue;
-            const C cv = Tr::mul(c6, v[e]);
-            const int x = gx0 + e;
-            // fire-and-forget reductions: one thread owns each face cell and issues
-            // its contributions in level order, so the rounding sequence is that of
-            // grad += c*lambda_S, += c*lambda_{S-1}, ... (deterministic) without the
-            // warp waiting for a read-modify-write round trip
-            if (f & 1u) atomicAdd(gacc + g.lin(0, gy, p), cv);
-            if (f & 2u) atomicAdd(gacc + g.lin(g.nx + 1, gy, p), cv);
-            if (f & 4u) atomicAdd(gacc + g.lin(x, 0, p), cv);
-            if (f & 8u) atomicAdd(gacc + g.lin(x, g.ny + 1, p), cv);
-            if (zlo) atomicAdd(gacc + g.lin(x, gy, 0), cv);
-            if (zhi) atomicAdd(gacc + g.lin(x, gy, g.nz + 1), cv);
+                for (int zf = 0; zf < 2; ++zf) {
+                    if (q != (zf == 0 ? 1 : g.nz)) continue;
+                    S* face = fb + 2 * fxs + 2 * fys + zf * (long long)g.nx * g.ny +
+                              (long long)(gy - 1) * g.nx + (gx0 - 1);
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (outxy[e]) face[e] = Tr::st(Tr::mul(c6, Tr::ld(plane_s[mycol + e])));
+                }
+            }
         }
     };
 
@@ -260,7 +282,6 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
             const Vec<S, V> t = *reinterpret_cast<const Vec<S, V>*>(ring + SLOT * PLANE + mycol);
 #pragma unroll
             for (int e = 0; e < V; ++e) r[0][NEW][e] = Tr::ld(t.v[e]);
-            if (MODE == MODE_ADJ) adj_acc(r[0][NEW], p0);
         }
         // ---- levels 1..T
 #pragma unroll
@@ -364,7 +385,6 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
                     o.v[e] = kExactStore ? Tr::st_exact(out[e]) : Tr::st(out[e]);
                 }
                 *reinterpret_cast<Vec<S, V>*>(lvl + ((s - 1) * 2 + PAR) * PLANE + mycol) = o;
-                if (MODE == MODE_ADJ) adj_acc(out, q);
             } else if (q >= kz0 && q < kz1) {
                 const long long o = g.plane * q + rowoff;
                 if (all_out) {
@@ -383,6 +403,17 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
         }
         __syncthreads();
         if (*s_abort) return false;
+        if constexpr (MODE == MODE_ADJ) {
+            // levels 0..T-1 of this step (the input of each transposed sweep); a tile
+            // off the x/y faces only works when plane 1 or nz is among its levels
+            const bool zstep = (p0 >= 1 && p0 - (T - 1) <= 1) || (p0 >= g.nz && p0 - (T - 1) <= g.nz);
+            if (nxy > 0 || zstep) {
+                adj_faces(ring + SLOT * PLANE, 0, p0);
+#pragma unroll
+                for (int s = 1; s < T; ++s)
+                    if (m >= s) adj_faces(lvl + ((s - 1) * 2 + PAR) * PLANE, s, p0 - s);
+            }
+        }
         // the slot of plane Zlo+m-1 is free now: refill it with plane Zlo+m-1+NS,
         // and the rho ring's next slot with rho of the same k (see rho_slots)
         if (tid == 0 && m >= 1 && issued < M) {

@@ -72,6 +72,28 @@ struct BF16 {
     __device__ __forceinline__ static C sixth() { return 0x1.555556p-3f; }
 };
 
+// Packed FP32 pairs (sm_100 family): two independent IEEE-754 round-to-nearest
+// additions or multiplications in one instruction, bit for bit the results of
+// the two scalar operations.
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long p, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(p));
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+
 // Padded grid geometry: cell (i,j,k) at i + px * (j + (ny+2) * k).
 struct Geom {
     int nx, ny, nz;

@@ -52,11 +52,15 @@ enum { MODE_PLAIN = 0, MODE_RHS = 1, MODE_ADJ = 2 };
 
 constexpr int kRing = 6;  // TMA ring slots (the unroll period)
 constexpr int kAccBaseTB = 16;  // EMU >= this: accumulator with EMU - 16 additions
+#ifndef JAC_PACKED_F32
+#define JAC_PACKED_F32 1
+#endif
+constexpr bool kPackedF32 = JAC_PACKED_F32 != 0;  // packed FP32 pairs in the level updates
 
 struct TBArgs {
     Geom g;
     void* dst;          // output grid of the pass (level T)
-    void* grad;         // unused (kept for the layout of the argument block)
+    void* grad;         // gradient grid (only the never-executed hook below names it)
     void* fbuf;         // MODE_ADJ: face buffer, c * lambda at face-adjacent cells
     long long fstride;  // MODE_ADJ: elements per sweep in fbuf (all six faces)
     int sweep0;         // MODE_ADJ: sweep index of this pass's level 0 in fbuf
@@ -248,10 +252,45 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
         }
     };
 
+    // Never executed: a per-level reduction hook (global reductions into the
+    // gradient grid, unreachable in every mode), called at every level of the
+    // k-march.  Kept because its presence changes how nvcc 13.0 schedules the
+    // k-march: measured on GB300 at 512^3, FP32 depth 3 runs at 993 GLUP/s with it
+    // and 792 without it (bf16 878 / 687; the same loss with an empty hook or with
+    // the hook's loop removed).  The reason is not known; the results are the same
+    // bits either way.
+    S* grad = static_cast<S*>(a.grad);
+    constexpr uint32_t fmask = 0;
+    constexpr bool xy_face = false;
+    auto adj_acc = [&](const C* v, int p) {
+        if constexpr (true) return;
+        const bool zlo = p == 1, zhi = p == g.nz;
+        if (FAST ? !(zlo || zhi) : (!xy_face && !(zlo || zhi))) return;
+        if (p < kz0 || p >= kz1 || fmask == 0u) return;
+        C* gacc = reinterpret_cast<C*>(grad);
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const uint32_t f = (fmask >> (5 * (V - 1 - e))) & 31u;
+            if (!(f & 16u)) continue;
+            const C cv = Tr::mul(c6, v[e]);
+            const int x = gx0 + e;
+            if (f & 1u) atomicAdd(gacc + g.lin(0, gy, p), cv);
+            if (f & 2u) atomicAdd(gacc + g.lin(g.nx + 1, gy, p), cv);
+            if (f & 4u) atomicAdd(gacc + g.lin(x, 0, p), cv);
+            if (f & 8u) atomicAdd(gacc + g.lin(x, g.ny + 1, p), cv);
+            if (zlo) atomicAdd(gacc + g.lin(x, gy, 0), cv);
+            if (zhi) atomicAdd(gacc + g.lin(x, gy, g.nz + 1), cv);
+        }
+    };
+
     // EMU >= kAccBaseTB (FP64 plain sweeps): the first EMU - kAccBaseTB additions
     // of every update through the exact accumulator of emusum.cuh instead
     constexpr bool kAcc = EMU >= kAccBaseTB && std::is_same<C, double>::value &&
                           MODE == MODE_PLAIN;
+    // FP32 arithmetic (FP32 and bf16 storage) on pairs of cells
+    // (FP32 storage, depths 1-2: measured 707 / 950 against 693 / 924 GLUP/s at 512^3;
+    // deeper kernels spill with it, and bf16 storage ran slower)
+    constexpr bool kPacked = kPackedF32 && std::is_same<S, float>::value && V % 2 == 0 && T <= 2;
     // addition number idx (0..4) of an update: the first EMU on the integer pipes
     const uint32_t one = a.one;
     auto add = [one](int idx, C x, C y) -> C {
@@ -282,6 +321,7 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
             const Vec<S, V> t = *reinterpret_cast<const Vec<S, V>*>(ring + SLOT * PLANE + mycol);
 #pragma unroll
             for (int e = 0; e < V; ++e) r[0][NEW][e] = Tr::ld(t.v[e]);
+            if (MODE == MODE_ADJ) adj_acc(r[0][NEW], p0);
         }
         // ---- levels 1..T
 #pragma unroll
@@ -346,6 +386,25 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
                         for (int i = K + 1; i <= 5; ++i) sum[e] = Tr::add(sum[e], x[e][i]);
                         val[e] = Tr::mul(sum[e], c6);
                     }
+                } else if constexpr (kPacked) {
+                    // FP32 arithmetic on cell pairs (e, e+1): the same operand order
+                    // per cell, two lanes of one packed instruction
+                    const unsigned long long c6p = f2_pack(c6, c6);
+#pragma unroll
+                    for (int e = 0; e < V; e += 2) {
+                        const C l0 = (e == 0) ? left : r[s - 1][CUR][e - 1];
+                        const C r1 = (e + 2 == V) ? right : r[s - 1][CUR][e + 2];
+                        unsigned long long sp =
+                            f2_add(f2_pack(l0, r[s - 1][CUR][e]),
+                                   f2_pack(r[s - 1][CUR][e + 1], r1));
+                        sp = f2_add(sp, f2_pack(Tr::ld(vn.v[e]), Tr::ld(vn.v[e + 1])));
+                        sp = f2_add(sp, f2_pack(Tr::ld(vs.v[e]), Tr::ld(vs.v[e + 1])));
+                        sp = f2_add(sp, f2_pack(r[s - 1][OLD][e], r[s - 1][OLD][e + 1]));
+                        sp = f2_add(sp, f2_pack(r[s - 1][NEW][e], r[s - 1][NEW][e + 1]));
+                        if (MODE == MODE_RHS)
+                            sp = f2_add(sp, f2_pack(Tr::ld(vr.v[e]), Tr::ld(vr.v[e + 1])));
+                        f2_unpack(f2_mul(sp, c6p), val[e], val[e + 1]);
+                    }
                 } else {
 #pragma unroll
                 for (int e = 0; e < V; ++e) {
@@ -385,6 +444,7 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
                     o.v[e] = kExactStore ? Tr::st_exact(out[e]) : Tr::st(out[e]);
                 }
                 *reinterpret_cast<Vec<S, V>*>(lvl + ((s - 1) * 2 + PAR) * PLANE + mycol) = o;
+                if (MODE == MODE_ADJ) adj_acc(out, q);
             } else if (q >= kz0 && q < kz1) {
                 const long long o = g.plane * q + rowoff;
                 if (all_out) {

@@ -358,13 +358,14 @@ def variant_batched(dev):
     from paper_0912_4506_gb300 import api, autotune, inputs
     specs = inputs.batch_specs()
     shapes = [s[:3] for s in specs]
-    ts, _ = autotune.tune(shapes, "f32")
+    choice, _ = autotune.tune(shapes, "f32")
     grids = []
     for i, (nx, ny, nz, n) in enumerate(specs):
         a = inputs.to_dtype(inputs.uniform_grid_f64(nx, ny, nz, g=i), "f32",
                             px=inputs.row_pitch(nx, "f32"))
         grids.append(api.from_numpy(a, nx, dev))
-    b = api.Batch(grids, [s[3] for s in specs], t=ts)
+    b = api.Batch(grids, [s[3] for s in specs], t=[c[1] for c in choice],
+                  tile_x=[c[0] for c in choice])
     b.run()
     torch.cuda.synchronize()
     reps = 3
@@ -380,12 +381,13 @@ def variant_batched(dev):
     lups = sum(nx * ny * nz * n for nx, ny, nz, n in specs)
     info = b.info()
     hist = {}
-    for t in info["t"]:
-        hist[str(t)] = hist.get(str(t), 0) + 1
+    for tx, t in zip(info["tile_x"], info["t"]):
+        k = f"{tx}x32_t{t}"
+        hist[k] = hist.get(k, 0) + 1
     b.close()
     return {"glups": round(lups / ms / 1e6, 2), "ms_per_run": round(ms, 3), "grids": len(specs),
             "lups_per_run": lups, "work_items": info["items"], "persistent_ctas": info["ctas"],
-            "depth_histogram": hist, "launches_per_run": 1}
+            "plan_histogram": hist, "launches_per_run": 1}
 
 
 def variant_adjoint(dev, n=256, nsweeps=50, t_fwd=3, t_adj=(("f32", 3), ("f64", 1))):

@@ -218,7 +218,10 @@ typedef struct jacobi_batch_s *jacobi_batch_t;
  * (elements, row a multiple of 16 bytes), grids_a[i]/grids_b[i] = caller-owned
  * device grids (A holds the initial grid and boundary layer; B receives A's
  * boundary layer here), nsweeps[i] >= 0, t[i] = depth (0 or t == NULL: 4;
- * at most 6), nchunk[i] = k-chunks per pass (0 or nchunk == NULL: planner).
+ * at most 6), tile_x[i] = width of the loaded tile in cells, 64 or 128 (128 only
+ * for depths up to 2; 0 or tile_x == NULL: 128 where the depth allows it, else
+ * 64), nchunk[i] = k-chunks per pass (0 or nchunk == NULL: planner).  A depth or
+ * width without a kernel gives JAC_EUNSUPPORTED.
  * Work items are (grid, pass, tile) in pass-round order; a CTA waits (bounded by
  * wait_limit_s, 0 = 2 s) for the previous pass of its grid.  The library owns the
  * descriptors, the work list and the counters (freed by jacobi_batch_destroy).
@@ -226,8 +229,8 @@ typedef struct jacobi_batch_s *jacobi_batch_t;
 JAC_API int jacobi_batch_create(jacobi_batch_t *out, int count, const int *dims,
                                 const long long *pitches, void *const *grids_a,
                                 void *const *grids_b, const int *nsweeps, const int *t,
-                                const int *nchunk, int dtype, void *stream, int flags,
-                                double wait_limit_s);
+                                const int *tile_x, const int *nchunk, int dtype, void *stream,
+                                int flags, double wait_limit_s);
 
 /* jacobi_batch_run — enqueue one run of the whole batch on the batch's stream
  * (every grid advances by its own sweep count from A).  final_is_b (count
@@ -236,10 +239,10 @@ JAC_API int jacobi_batch_create(jacobi_batch_t *out, int count, const int *dims,
  * wherever the first left A (the result itself when it ended in A). */
 JAC_API int jacobi_batch_run(jacobi_batch_t b, int *final_is_b);
 
-/* jacobi_batch_info — per grid: depth used and number of passes; totals: work
- * items and persistent CTAs.  Any pointer may be NULL. */
-JAC_API int jacobi_batch_info(jacobi_batch_t b, int *t_used, int *passes, int *items,
-                              int *ctas);
+/* jacobi_batch_info — per grid: depth used, tile width and number of passes;
+ * totals: work items and persistent CTAs.  Any pointer may be NULL. */
+JAC_API int jacobi_batch_info(jacobi_batch_t b, int *t_used, int *tile_x, int *passes,
+                              int *items, int *ctas);
 
 /* jacobi_batch_check — wait for the batch's stream; JAC_ETIMEOUT if a bounded
  * device wait ran out during a run. */

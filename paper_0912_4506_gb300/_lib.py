@@ -73,9 +73,9 @@ def load(path=None):
         "jacobi_version": ([], I),
         "jacobi_sweep_noalloc": ([I, I, I, I, P, LL, I, I, P, I], I),
         "jacobi_batch_create": ([ctypes.POINTER(P), I, PI, ctypes.POINTER(LL), ctypes.POINTER(P),
-                                 ctypes.POINTER(P), PI, PI, PI, I, P, I, ctypes.c_double], I),
+                                 ctypes.POINTER(P), PI, PI, PI, PI, I, P, I, ctypes.c_double], I),
         "jacobi_batch_run": ([P, PI], I),
-        "jacobi_batch_info": ([P, PI, PI, PI, PI], I),
+        "jacobi_batch_info": ([P, PI, PI, PI, PI, PI], I),
         "jacobi_batch_check": ([P], I),
         "jacobi_batch_destroy": ([P], I),
         "jacobi_emulated_add": ([P, P, P, LL, P], I),
@@ -189,7 +189,7 @@ def _ints(v):
 
 
 def jacobi_batch_create(dims, pitches, grids_a, grids_b, nsweeps, t, nchunk, dtype, stream,
-                        flags=0, wait_limit_s=0.0):
+                        flags=0, wait_limit_s=0.0, tile_x=None):
     """dims: list of (nx, ny, nz); the other lists have one entry per grid."""
     n = len(dims)
     h = ctypes.c_void_p()
@@ -198,8 +198,8 @@ def jacobi_batch_create(dims, pitches, grids_a, grids_b, nsweeps, t, nchunk, dty
     rc = load().jacobi_batch_create(
         ctypes.byref(h), n, _ints(flat), (ctypes.c_longlong * n)(*pitches),
         (P * n)(*grids_a), (P * n)(*grids_b), _ints(nsweeps),
-        _ints(t) if t is not None else None, _ints(nchunk) if nchunk is not None else None,
-        dtype, stream, flags, float(wait_limit_s))
+        _ints(t) if t is not None else None, _ints(tile_x) if tile_x is not None else None,
+        _ints(nchunk) if nchunk is not None else None, dtype, stream, flags, float(wait_limit_s))
     _ck(rc, "jacobi_batch_create")
     return h
 
@@ -212,12 +212,14 @@ def jacobi_batch_run(h, count):
 
 def jacobi_batch_info(h, count):
     t = (ctypes.c_int * count)()
+    tx = (ctypes.c_int * count)()
     p = (ctypes.c_int * count)()
     items = ctypes.c_int(0)
     ctas = ctypes.c_int(0)
-    _ck(load().jacobi_batch_info(h, t, p, ctypes.byref(items), ctypes.byref(ctas)),
+    _ck(load().jacobi_batch_info(h, t, tx, p, ctypes.byref(items), ctypes.byref(ctas)),
         "jacobi_batch_info")
-    return {"t": list(t), "passes": list(p), "items": items.value, "ctas": ctas.value}
+    return {"t": list(t), "tile_x": list(tx), "passes": list(p), "items": items.value,
+            "ctas": ctas.value}
 
 
 def jacobi_batch_check(h):

@@ -381,13 +381,14 @@ class Batch:
 
     ``grids``: list of float32 or bfloat16 grids (each its own shape); ``nsweeps``:
     sweeps per grid; ``t``: depth per grid (None: 4, or the autotuner's choice);
-    ``nchunk``: k-chunks per pass per grid (None: planner).  B grids are allocated
+    ``tile_x``: loaded tile width per grid, 64 or 128 (None: 128 where the depth
+    allows it); ``nchunk``: k-chunks per pass per grid (None: planner).  B grids are allocated
     with each A's layout.  ``run()`` returns the list of tensors holding the
     results.
     """
 
     def __init__(self, grids, nsweeps, t=None, nchunk=None, graph=True, test_missing_producer=False,
-                 wait_limit_s=0.0):
+                 wait_limit_s=0.0, tile_x=None):
         if not grids:
             raise ValueError("empty batch")
         dt = grids[0].dtype
@@ -403,7 +404,7 @@ class Batch:
             self._h = _lib.jacobi_batch_create(
                 [g[:3] for g in geo], [g[3] for g in geo], [a.data_ptr() for a in self.A],
                 [b.data_ptr() for b in self.B], list(nsweeps), t, nchunk, _DT[dt],
-                _stream_ptr(self.device), flags, wait_limit_s)
+                _stream_ptr(self.device), flags, wait_limit_s, tile_x)
         self.count = len(grids)
 
     def run(self):

@@ -1,8 +1,8 @@
-"""Autotuner for the temporal-blocking depth (and k-chunking) of batched grids.
+"""Autotuner for the tile shape and temporal-blocking depth of batched grids.
 
 For every distinct grid shape it times the batched persistent kernel itself on
-enough replicas of that shape to fill the GPU, for each candidate depth, and
-keeps the fastest (lattice-site updates per second).  Results are cached in a
+enough replicas of that shape to fill the GPU, for each candidate (tile width,
+depth), and keeps the fastest (lattice-site updates per second).  Results are cached in a
 JSON file keyed by device name, dtype and shape, so a batch is tuned once.
 The paper chose its blocking parameters experimentally as well (Sect. 1.4: the
 parameter space is large and the best values were found by measurement).
@@ -15,7 +15,8 @@ import torch
 
 from . import api
 
-DEFAULT_CANDIDATES = (2, 3, 4, 5, 6)
+# (loaded tile width, depth): 128-wide tiles exist up to depth 2, 64-wide up to 6
+DEFAULT_CANDIDATES = ((128, 1), (128, 2), (64, 2), (64, 3), (64, 4), (64, 5), (64, 6))
 
 
 def cache_path():
@@ -37,14 +38,15 @@ def _key(dev, dtype, shape):
     return f"{torch.cuda.get_device_name(dev)}|{dtype}|{shape[0]}x{shape[1]}x{shape[2]}"
 
 
-def _time_shape(shape, dtype, t, sweeps, device, reps):
+def _time_shape(shape, dtype, cand, sweeps, device, reps):
+    tile_x, t = cand
     nx, ny, nz = shape
     grids = []
     for _ in range(reps):
         g = api.alloc_grid(nx, ny, nz, dtype, device)
         g.uniform_()
         grids.append(g)
-    b = api.Batch(grids, [sweeps] * reps, t=[t] * reps)
+    b = api.Batch(grids, [sweeps] * reps, t=[t] * reps, tile_x=[tile_x] * reps)
     b.run()  # warm-up
     torch.cuda.synchronize(device)
     t0 = time.perf_counter()
@@ -58,7 +60,8 @@ def _time_shape(shape, dtype, t, sweeps, device, reps):
 
 def tune(shapes, dtype="f32", candidates=DEFAULT_CANDIDATES, sweeps=24, device="cuda",
          use_cache=True):
-    """Best depth per shape (list aligned with `shapes`) and the measurements."""
+    """Best (tile width, depth) per shape (list aligned with `shapes`) and the
+    measurements."""
     path = cache_path()
     cache = _load(path) if use_cache else {}
     dev = torch.device(device)
@@ -66,17 +69,19 @@ def tune(shapes, dtype="f32", candidates=DEFAULT_CANDIDATES, sweeps=24, device="
     out, table = [], {}
     for shape in shapes:
         key = _key(dev, dtype, shape)
-        if key in cache:
-            out.append(cache[key]["t"])
+        if key in cache and "tile_x" in cache[key]:
+            out.append((cache[key]["tile_x"], cache[key]["t"]))
             table[key] = cache[key]
             continue
         nx, ny, nz = shape
         cells = nx * ny * nz
         # replicas: enough tiles to cover every SM a few times, bounded memory
         reps = max(1, min(64, (4 * sms * 64 * 32) // max(cells // 8, 1) + 1))
-        rates = {t: _time_shape(shape, dtype, t, sweeps, dev, reps) for t in candidates}
+        rates = {tuple(c): _time_shape(shape, dtype, tuple(c), sweeps, dev, reps)
+                 for c in candidates}
         best = max(rates, key=rates.get)
-        cache[key] = {"t": best, "glups": {str(k): v / 1e9 for k, v in rates.items()}}
+        cache[key] = {"tile_x": best[0], "t": best[1],
+                      "glups": {f"{k[0]}x{k[1]}": v / 1e9 for k, v in rates.items()}}
         table[key] = cache[key]
         out.append(best)
     if use_cache:

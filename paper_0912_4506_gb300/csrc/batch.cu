@@ -35,7 +35,7 @@ struct jacobi_batch_s {
     int count = 0, dtype = 0, device = 0, num_sms = 0;
     cudaStream_t stream = nullptr;
     std::vector<BatchGridDesc> host_desc;
-    std::vector<int> final_b, t_used, passes;
+    std::vector<int> final_b, t_used, passes, tile_x;
     int nitems = 0, ctas = 0;
     size_t smem = 0;
     BatchGridDesc* d_desc = nullptr;
@@ -52,11 +52,12 @@ namespace {
 
 // Tile geometry of a pass of depth t; the k-chunk count keeps chunks >= 8t planes
 // (many grids share the GPU, so no grid needs whole waves of its own).
-BatchPassGeom pass_geom(const Geom& g, int dtype, int t, int nchunk_req) {
+BatchPassGeom pass_geom(const Geom& g, int dtype, int t, int v, int nchunk_req) {
     const int nchunk = nchunk_req > 0 ? nchunk_req : std::max(1, g.nz / std::max(8 * t, 32));
-    const TileGeom tg = tile_geom(dtype, g, kBatchV, kBatchNW, t, 1, nchunk);
+    const TileGeom tg = tile_geom(dtype, g, v, kBatchNW, t, 1, nchunk);
     BatchPassGeom p{};
     p.t = t;
+    p.v = v;
     p.ox = tg.ox;
     p.x0_first = tg.x0_first;
     p.ntx = tg.ntx;
@@ -98,7 +99,8 @@ extern "C" {
 
 int jacobi_batch_create(jacobi_batch_t* out, int count, const int* dims,
                         const long long* pitches, void* const* grids_a, void* const* grids_b,
-                        const int* nsweeps, const int* t, const int* nchunk, int dtype,
+                        const int* nsweeps, const int* t, const int* tile_x, const int* nchunk,
+                        int dtype,
                         void* stream, int flags, double wait_limit_s) {
     if (!out) return JAC_EINVAL;
     *out = nullptr;
@@ -124,6 +126,7 @@ int jacobi_batch_create(jacobi_batch_t* out, int count, const int* dims,
     b->final_b.resize(count);
     b->t_used.resize(count);
     b->passes.resize(count);
+    b->tile_x.resize(count);
     int max_pass = 0;
     for (int i = 0; i < count; ++i) {
         const int nx = dims[3 * i], ny = dims[3 * i + 1], nz = dims[3 * i + 2];
@@ -142,6 +145,13 @@ int jacobi_batch_create(jacobi_batch_t* out, int count, const int* dims,
         }
         int ti = (t && t[i] > 0) ? t[i] : 4;
         ti = std::min(ti, std::max(1, nsweeps[i]));
+        // tile width: the caller's (64 or 128), else 128 where the depth allows it
+        const int tx = (tile_x && tile_x[i] > 0) ? tile_x[i] : (ti <= kBatchTMaxWide ? 128 : 64);
+        if ((tx != 64 && tx != 128) || (tx == 128 && ti > kBatchTMaxWide)) {
+            delete b;
+            return JAC_EUNSUPPORTED;  // no kernel for this tile width and depth
+        }
+        const int vi = tx / 32;
         const int nc = nchunk ? nchunk[i] : 0;
         BatchGridDesc& d = b->host_desc[i];
         d.g = g;
@@ -150,14 +160,15 @@ int jacobi_batch_create(jacobi_batch_t* out, int count, const int* dims,
         const int n = nsweeps[i];
         d.npass = (n + ti - 1) / ti;
         const int rem = n - (d.npass - 1) * ti;
-        d.full = pass_geom(g, dtype, ti, nc);
-        d.last = pass_geom(g, dtype, n > 0 ? rem : ti, nc);
+        d.full = pass_geom(g, dtype, ti, vi, nc);
+        d.last = pass_geom(g, dtype, n > 0 ? rem : ti, vi, nc);
         b->final_b[i] = d.npass & 1;
         b->t_used[i] = ti;
+        b->tile_x[i] = tx;
         b->passes[i] = d.npass;
         max_pass = std::max(max_pass, d.npass);
-        if (!encode_grid_map(&maps[2 * i], dtype, g, grids_a[i], 32 * kBatchV, kBatchNW) ||
-            !encode_grid_map(&maps[2 * i + 1], dtype, g, grids_b[i], 32 * kBatchV, kBatchNW)) {
+        if (!encode_grid_map(&maps[2 * i], dtype, g, grids_a[i], tx, kBatchNW) ||
+            !encode_grid_map(&maps[2 * i + 1], dtype, g, grids_b[i], tx, kBatchNW)) {
             delete b;
             return JAC_ECUDA;
         }
@@ -187,8 +198,12 @@ int jacobi_batch_create(jacobi_batch_t* out, int count, const int* dims,
     b->nitems = (int)items.size();
 
     const void* kern = batch_kernel_ptr(dtype);
-    b->smem = (dtype == JAC_F32) ? TBLayout<kBatchV, kBatchNW, kBatchTMax, kRing, float>::bytes()
-                                 : TBLayout<kBatchV, kBatchNW, kBatchTMax, kRing, uint16_t>::bytes();
+    // shared memory: the larger of the two tile families' deepest layouts
+    b->smem = (dtype == JAC_F32)
+                  ? std::max(TBLayout<2, kBatchNW, kBatchTMax, kRing, float>::bytes(),
+                             TBLayout<4, kBatchNW, kBatchTMaxWide, kRing, float>::bytes())
+                  : std::max(TBLayout<2, kBatchNW, kBatchTMax, kRing, uint16_t>::bytes(),
+                             TBLayout<4, kBatchNW, kBatchTMaxWide, kRing, uint16_t>::bytes());
     int occ = 0;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem) !=
             cudaSuccess ||
@@ -271,10 +286,12 @@ int jacobi_batch_run(jacobi_batch_t b, int* final_is_b) {
     return JAC_OK;
 }
 
-int jacobi_batch_info(jacobi_batch_t b, int* t_used, int* passes, int* items, int* ctas) {
+int jacobi_batch_info(jacobi_batch_t b, int* t_used, int* tile_x, int* passes, int* items,
+                      int* ctas) {
     if (!b) return JAC_EINVAL;
     for (int i = 0; i < b->count; ++i) {
         if (t_used) t_used[i] = b->t_used[i];
+        if (tile_x) tile_x[i] = b->tile_x[i];
         if (passes) passes[i] = b->passes[i];
     }
     if (items) *items = b->nitems;

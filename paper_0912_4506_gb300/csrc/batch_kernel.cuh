@@ -5,10 +5,13 @@
 
 namespace jac {
 
-constexpr int kBatchV = 2, kBatchNW = 32, kBatchTMax = 6;
+// Every CTA has 32 warps (one row each); a grid's tiles are 64 (V = 2, depths
+// 1-6) or 128 (V = 4, depths 1-2) cells wide -- deeper 128-wide tiles need more
+// registers than 1024-thread CTAs of this kernel have (they spill).
+constexpr int kBatchNW = 32, kBatchTMax = 6, kBatchTMaxWide = 2;
 
 struct BatchPassGeom {
-    int t, ox, x0_first, ntx, nty, kz, nchunk;
+    int t, v, ox, x0_first, ntx, nty, kz, nchunk;
 };
 
 struct BatchGridDesc {
@@ -45,15 +48,14 @@ __device__ __forceinline__ void fence_proxy_async_global() {
     asm volatile("fence.proxy.async.global;" ::: "memory");
 }
 
-template <class Tr, int T>
+template <class Tr, int V, int T>
 __device__ __forceinline__ void batch_tile(const CUtensorMap* map, const TBArgs& a, int bx,
                                            int by, int bz, unsigned char* smem, int* s_abort) {
-    if (tile_inside_xy<kBatchV, kBatchNW, T>(a, bx, by))
-        tb_tile<Tr, kBatchV, kBatchNW, T, MODE_PLAIN, true>(map, nullptr, a, bx, by, bz, smem,
-                                                            s_abort);
+    if (tile_inside_xy<V, kBatchNW, T>(a, bx, by))
+        tb_tile<Tr, V, kBatchNW, T, MODE_PLAIN, true>(map, nullptr, a, bx, by, bz, smem, s_abort);
     else
-        tb_tile<Tr, kBatchV, kBatchNW, T, MODE_PLAIN, false>(map, nullptr, a, bx, by, bz, smem,
-                                                             s_abort);
+        tb_tile<Tr, V, kBatchNW, T, MODE_PLAIN, false>(map, nullptr, a, bx, by, bz, smem,
+                                                       s_abort);
 }
 
 template <class Tr>
@@ -106,13 +108,21 @@ __global__ void __launch_bounds__(kBatchNW * 32, 1) tb_batch_kernel(const BatchA
         const int by = (item.tile / pg.ntx) % pg.nty;
         const int bz = item.tile / (pg.ntx * pg.nty);
         const CUtensorMap* map = ba.maps + 2 * item.g + (item.pass & 1);
-        switch (pg.t) {
-            case 1: batch_tile<Tr, 1>(map, a, bx, by, bz, smem, &s_abort); break;
-            case 2: batch_tile<Tr, 2>(map, a, bx, by, bz, smem, &s_abort); break;
-            case 3: batch_tile<Tr, 3>(map, a, bx, by, bz, smem, &s_abort); break;
-            case 4: batch_tile<Tr, 4>(map, a, bx, by, bz, smem, &s_abort); break;
-            case 5: batch_tile<Tr, 5>(map, a, bx, by, bz, smem, &s_abort); break;
-            default: batch_tile<Tr, 6>(map, a, bx, by, bz, smem, &s_abort); break;
+        if (pg.v == 4) {
+            switch (pg.t) {
+                case 1: batch_tile<Tr, 4, 1>(map, a, bx, by, bz, smem, &s_abort); break;
+
+                default: batch_tile<Tr, 4, 2>(map, a, bx, by, bz, smem, &s_abort); break;
+            }
+        } else {
+            switch (pg.t) {
+                case 1: batch_tile<Tr, 2, 1>(map, a, bx, by, bz, smem, &s_abort); break;
+                case 2: batch_tile<Tr, 2, 2>(map, a, bx, by, bz, smem, &s_abort); break;
+                case 3: batch_tile<Tr, 2, 3>(map, a, bx, by, bz, smem, &s_abort); break;
+                case 4: batch_tile<Tr, 2, 4>(map, a, bx, by, bz, smem, &s_abort); break;
+                case 5: batch_tile<Tr, 2, 5>(map, a, bx, by, bz, smem, &s_abort); break;
+                default: batch_tile<Tr, 2, 6>(map, a, bx, by, bz, smem, &s_abort); break;
+            }
         }
         // publish: every thread's stores of this tile are made visible at GPU
         // scope before the one release on the grid's completion counter

@@ -288,9 +288,11 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
     constexpr bool kAcc = EMU >= kAccBaseTB && std::is_same<C, double>::value &&
                           MODE == MODE_PLAIN;
     // FP32 arithmetic (FP32 and bf16 storage) on pairs of cells
-    // (FP32 storage, depths 1-2: measured 707 / 950 against 693 / 924 GLUP/s at 512^3;
-    // deeper kernels spill with it, and bf16 storage ran slower)
-    constexpr bool kPacked = kPackedF32 && std::is_same<S, float>::value && V % 2 == 0 && T <= 2;
+    // (FP32 storage, depths 1-2, CTAs of at most 16 warps: measured 707 / 950 against
+    // 693 / 924 GLUP/s at 512^3; deeper or 1024-thread kernels spill with it, and
+    // bf16 storage ran slower)
+    constexpr bool kPacked = kPackedF32 && std::is_same<S, float>::value && V % 2 == 0 &&
+                             T <= 2 && NW <= 16;
     // addition number idx (0..4) of an update: the first EMU on the integer pipes
     const uint32_t one = a.one;
     auto add = [one](int idx, C x, C y) -> C {

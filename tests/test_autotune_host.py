@@ -17,21 +17,25 @@ def test_tune_measures_once_then_uses_cache(tmp_path, monkeypatch):
                         lambda dev=None: types.SimpleNamespace(multi_processor_count=152))
     calls = []
 
-    def fake_time(shape, dtype, t, sweeps, device, reps):
-        calls.append((shape, t))
-        best = 4 if shape[0] >= 100 else 2  # rate peaks at the shape's best depth
-        return 1e9 * (10.0 - abs(t - best))
+    def fake_time(shape, dtype, cand, sweeps, device, reps):
+        calls.append((shape, cand))
+        tile_x, t = cand
+        # rate peaks at the shape's best (width, depth)
+        best = (128, 3) if shape[0] >= 100 else (64, 2)
+        return 1e9 * (10.0 - abs(t - best[1]) - (0 if tile_x == best[0] else 0.5))
 
     monkeypatch.setattr(autotune, "_time_shape", fake_time)
     shapes = [(128, 64, 64), (40, 40, 40), (128, 64, 64)]
-    ts, table = autotune.tune(shapes, "f32", candidates=(2, 3, 4, 5), device="cpu")
-    assert ts == [4, 2, 4]
+    cands = ((128, 2), (128, 3), (64, 2), (64, 3))
+    ts, table = autotune.tune(shapes, "f32", candidates=cands, device="cpu")
+    assert ts == [(128, 3), (64, 2), (128, 3)]
     # two distinct shapes x four candidates (the repeated shape is measured once)
     assert len(calls) == 8
     cached = json.loads((tmp_path / "autotune.json").read_text())
-    assert cached["FakeGPU|f32|128x64x64"]["t"] == 4
+    assert (cached["FakeGPU|f32|128x64x64"]["tile_x"], cached["FakeGPU|f32|128x64x64"]["t"]) \
+        == (128, 3)
     assert cached["FakeGPU|f32|40x40x40"]["t"] == 2
 
     calls.clear()
-    ts2, _ = autotune.tune(shapes, "f32", candidates=(2, 3, 4, 5), device="cpu")
+    ts2, _ = autotune.tune(shapes, "f32", candidates=cands, device="cpu")
     assert ts2 == ts and calls == []

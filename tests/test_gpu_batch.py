@@ -26,14 +26,21 @@ def _make(dtype, specs, g0=0):
 
 
 @pytest.mark.parametrize("dtype", ["f32", "bf16"])
-@pytest.mark.parametrize("graph", [True, False])
-def test_batch_bit_exact_vs_oracle(dtype, graph):
+@pytest.mark.parametrize("graph,wide", [(True, None), (False, None), (True, 64)])
+def test_batch_bit_exact_vs_oracle(dtype, graph, wide):
+    """Default widths (128-wide tiles for depths 1-2, 64 otherwise) and all grids
+    on 64-wide tiles."""
     from paper_0912_4506_gb300 import api
     hosts, grids = _make(dtype, SPECS)
-    b = api.Batch(grids, [s[1] for s in SPECS], t=[s[2] for s in SPECS], graph=graph)
+    tx = None if wide is None else [wide] * len(SPECS)
+    b = api.Batch(grids, [s[1] for s in SPECS], t=[s[2] for s in SPECS], graph=graph,
+                  tile_x=tx)
     outs = b.run()
     b.check()
     info = b.info()
+    want_tx = [(128 if max(1, min(s[2], max(1, s[1]))) <= 2 else 64) if wide is None else wide
+               for s in SPECS]
+    assert info["tile_x"] == want_tx
     for (shape, n, t), a, out, tu in zip(SPECS, hosts, outs, info["t"]):
         nx = shape[0]
         want = oracle.sweeps(a, n, nx=nx, dtype=dtype)[:, :, :nx + 2]
@@ -114,7 +121,19 @@ def test_batch_workload_64_grids_vs_single_path():
 def test_autotuner_picks_a_candidate(tmp_path, monkeypatch):
     from paper_0912_4506_gb300 import autotune
     monkeypatch.setenv("JACOBI_GB300_CACHE", str(tmp_path))
-    best, table = autotune.tune([(64, 48, 40), (32, 32, 32)], candidates=(2, 4), sweeps=8)
-    assert all(t in (2, 4) for t in best)
-    again, _ = autotune.tune([(64, 48, 40)], candidates=(2, 4), sweeps=8)
+    cands = ((128, 2), (64, 4))
+    best, table = autotune.tune([(64, 48, 40), (32, 32, 32)], candidates=cands, sweeps=8)
+    assert all(tuple(c) in cands for c in best)
+    again, _ = autotune.tune([(64, 48, 40)], candidates=cands, sweeps=8)
     assert again[0] == best[0]  # served from the cache
+
+
+def test_wide_tiles_deeper_than_built_rejected():
+    from paper_0912_4506_gb300 import _lib, api
+    hosts, grids = _make("f32", SPECS[:2])
+    with pytest.raises(_lib.JacobiError) as ei:
+        api.Batch(grids, [10, 10], t=[3, 2], tile_x=[128, 128])
+    assert ei.value.code == _lib.JAC_EUNSUPPORTED
+    with pytest.raises(_lib.JacobiError) as ei:
+        api.Batch(grids, [10, 10], t=[7, 2])
+    assert ei.value.code == _lib.JAC_EUNSUPPORTED

@@ -38,6 +38,14 @@ ALGO_BYTES_PER_LUP = {"f64": 16, "f32": 8, "bf16": 4}
 # update, no re-reads).  A kernel without a capture of its current code: None.
 TRAFFIC_PER_LAUNCH = {}
 
+# Instructions per computed cell update of the blocked kernels, read from ncu
+# captures of the FP32 and bf16 depth-3 kernels at 384^3 (warp instructions per
+# useful update x 32 / computed-per-useful cells) and of the FP64 sweep with the
+# integer-pipe accumulator; inputs of the performance model (model.py), beside
+# the measured HBM bandwidth and pipe rates.
+MODEL_INST_PER_UPDATE = {"f32": 17.0, "bf16": 23.4, "f64": 150.0}
+MODEL_FP64_OPS_PER_UPDATE = 2  # the FP64-unit share of an accumulator update
+
 # Pipe-rate probes (jacobi_pipe_probe): launch shape and operations per update of
 # the FP64 sweep with 3 of its 5 additions on the integer pipes.
 PROBE_BLOCKS_PER_SM, PROBE_THREADS = 8, 256
@@ -62,6 +70,9 @@ def parse():
     p.add_argument("--kernel", default="auto", choices=["auto", "plain", "tb"])
     p.add_argument("--size", type=int, default=NX)
     p.add_argument("--sweeps", type=int, default=NSWEEPS)
+    p.add_argument("--slabs", action="store_true",
+                   help="with N ranks: one z-slab of a 512 x 512 x (512 N) FP64 grid per rank, "
+                        "halos exchanged by NCCL send/recv (weak scaling), instead of replicas")
     return p.parse_args()
 
 
@@ -260,13 +271,13 @@ def time_sweeps(j, nsweeps, t, kernel, steps, warmup, stream):
     return e0.elapsed_time(e1) / steps
 
 
-def variant_rows(dev, steps):
+def variant_rows(dev, steps, model_in=None):
     """GLUP/s of every kernel family and depth on the same GPU, beside the plain
     form (keys name the depth actually run; a depth with no kernel is recorded as
     not built, from the library's own rejection).  FP64 rows also state the
     multiple of the plain FP64 sweep."""
     import torch
-    from paper_0912_4506_gb300 import _lib, api
+    from paper_0912_4506_gb300 import _lib, api, model
     rows = {}
     stream = torch.cuda.current_stream()
     for dtype in ("f64", "f32", "bf16"):
@@ -291,8 +302,19 @@ def variant_rows(dev, steps):
                    "tile": [plan["ext_x"], plan["ext_y"]], "emu_adds": plan["emu_adds"]}
             if name == "plain":
                 plain_glups = glups
-            elif dtype == "f64" and plain_glups:
-                row["multiple_of_plain"] = round(glups / plain_glups, 3)
+            else:
+                if dtype == "f64" and plain_glups:
+                    row["multiple_of_plain"] = round(glups / plain_glups, 3)
+                if model_in is not None:
+                    es = {"f64": 8, "f32": 4, "bf16": 2}[dtype]
+                    pred, bound = model.predict(
+                        plan["t"], plan["ext_x"], plan["ext_y"], es, model_in["hbm_gbs"],
+                        model_in["sm_mhz"], model_in["sms"], MODEL_INST_PER_UPDATE[dtype],
+                        kz=plan["kchunk"],
+                        pipe_ops=MODEL_FP64_OPS_PER_UPDATE if dtype == "f64" else 0.0,
+                        pipe_gops=model_in.get("dadd_gops"), nxy=(NX, NY))
+                    row["model_glups"] = round(pred, 1)
+                    row["model_bound"] = bound
             rows[f"{dtype}_{name}"] = row
         j.close()
         del j
@@ -351,14 +373,19 @@ def variant_precision(dev, n=1024, outer=20, inner=50, t=(("f32", 4), ("bf16", 2
     return rows
 
 
-def variant_batched(dev):
+def variant_batched(dev, model_in=None):
     """64 FP32 grids (shapes multiples of 8 in [32,256], sweeps in [10,200], seed 2),
     depth per grid from the autotuner, one persistent launch in a CUDA graph."""
     import torch
     from paper_0912_4506_gb300 import api, autotune, inputs
     specs = inputs.batch_specs()
     shapes = [s[:3] for s in specs]
-    choice, _ = autotune.tune(shapes, "f32")
+    params = None if model_in is None else {
+        "hbm_gbs": model_in["hbm_gbs"], "sm_mhz": model_in["sm_mhz"], "sms": model_in["sms"],
+        "inst_per_update": MODEL_INST_PER_UPDATE["f32"]}
+    # the model orders every shape's (width, depth) candidates; all but its last
+    # are timed (the model is a ceiling, not a fit: pruning deeper lost good picks)
+    choice, _ = autotune.tune(shapes, "f32", model_params=params, keep=6)
     grids = []
     for i, (nx, ny, nz, n) in enumerate(specs):
         a = inputs.to_dtype(inputs.uniform_grid_f64(nx, ny, nz, g=i), "f32",
@@ -620,9 +647,12 @@ def run_ours(args):
     del j
     torch.cuda.empty_cache()
     if world == 1 and not args.no_variants:
-        line["variants"] = variant_rows(dev, max(2, min(args.steps, 3)))
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        model_in = {"hbm_gbs": pk["hbm_gbs"], "sm_mhz": pk.get("sm_max_mhz", 2070.0),
+                    "sms": sms, "dadd_gops": pipes["dadd_gops"]}
+        line["variants"] = variant_rows(dev, max(2, min(args.steps, 3)), model_in)
+        line["batched_64"] = variant_batched(dev, model_in)
         line["precision_1024"] = variant_precision(dev)
-        line["batched_64"] = variant_batched(dev)
         line["adjoint_256"] = variant_adjoint(dev)
         line["slabs_512"] = variant_slabs(dev)
     if world == 1 and not args.no_cpu_baseline:
@@ -630,6 +660,65 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": round(rate, 4), "unit": "GLUP/s", "cores": cores,
                                 "kind": "oracle", "sample": sample}
     print(json.dumps(line), flush=True)
+
+
+def run_slabs(args):
+    """The z-slab decomposition across ranks (Sect. 2.1): a 512 x 512 x (512 N) FP64
+    grid, one slab of 512 core planes per rank, h = 4 halo planes exchanged with
+    the neighbouring ranks by NCCL send/recv every 4 sweeps (5 planes per side),
+    the sweeps in between the library's FP64 choice (plain sweeps, depth --t),
+    100 sweeps per step.  value = all ranks' lattice-site updates / max-over-ranks
+    time (weak scaling)."""
+    import torch
+    import torch.distributed as dist
+    from paper_0912_4506_gb300 import inputs, slabs
+    world, rank, local = dist_setup()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    h = 4
+    kt = args.t if args.t > 0 else 1
+    nzg = NZ * world
+    z0, z1 = slabs.slab_ranges(nzg, world)[rank]
+    lo, hi = slabs.slab_extent(z0, z1, nzg, h)
+    a = inputs.uniform_grid_f64(NX, NY, nzg, px=inputs.row_pitch(NX, "f64"), planes=(lo, hi))
+    rs = slabs.RankSlab(NX, NY, nzg, h, torch.from_numpy(a).to(dev), rank, world)
+    del a
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(args.warmup):
+        rs.sweep(NSWEEPS, h, kt)
+    torch.cuda.synchronize()
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        rs.sweep(NSWEEPS, h, kt)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    lups = NX * NY * NZ * NSWEEPS  # per rank
+    ms, _ = replica_throughput(e0.elapsed_time(e1), lups * args.steps, dev)
+    value = lups * world * args.steps / (ms / 1e3) / 1e9
+    rs.close()
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": round(value, 3), "unit": "GLUP/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"jacobi7pt_512x512x{nzg}_fp64_100sweeps_zslabs",
+                       "nx": NX, "ny": NY, "nz": nzg, "sweeps_per_step": NSWEEPS,
+                       "parallelism": f"z-slabs x {world}", "halo_planes": h,
+                       "sweep_depth": kt,
+                       "l2": "inputs larger than L2"}}), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
 
 
 def run_case(args):
@@ -760,5 +849,7 @@ if __name__ == "__main__":
         run_case(a)
     elif a.impl == "reference":
         run_reference(a)
+    elif a.slabs:
+        run_slabs(a)
     else:
         run_ours(a)

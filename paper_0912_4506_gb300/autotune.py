@@ -59,9 +59,13 @@ def _time_shape(shape, dtype, cand, sweeps, device, reps):
 
 
 def tune(shapes, dtype="f32", candidates=DEFAULT_CANDIDATES, sweeps=24, device="cuda",
-         use_cache=True):
+         use_cache=True, model_params=None, keep=None):
     """Best (tile width, depth) per shape (list aligned with `shapes`) and the
-    measurements."""
+    measurements.  With `model_params` (hbm_gbs, sm_mhz, sms, inst_per_update)
+    the candidates of each shape are ordered by the performance model (model.py,
+    the paper's Eq. 4-5 restated for the GPU) and only the first `keep` are
+    measured."""
+    from . import model
     path = cache_path()
     cache = _load(path) if use_cache else {}
     dev = torch.device(device)
@@ -77,11 +81,17 @@ def tune(shapes, dtype="f32", candidates=DEFAULT_CANDIDATES, sweeps=24, device="
         cells = nx * ny * nz
         # replicas: enough tiles to cover every SM a few times, bounded memory
         reps = max(1, min(64, (4 * sms * 64 * 32) // max(cells // 8, 1) + 1))
-        rates = {tuple(c): _time_shape(shape, dtype, tuple(c), sweeps, dev, reps)
-                 for c in candidates}
+        cands = [tuple(c) for c in candidates]
+        if model_params is not None:
+            es = {"f32": 4, "bf16": 2}[dtype]
+            cands = model.order_candidates(cands, shape, es, **model_params)
+            if keep:
+                cands = cands[:keep]
+        rates = {c: _time_shape(shape, dtype, c, sweeps, dev, reps) for c in cands}
         best = max(rates, key=rates.get)
         cache[key] = {"tile_x": best[0], "t": best[1],
-                      "glups": {f"{k[0]}x{k[1]}": v / 1e9 for k, v in rates.items()}}
+                      "glups": {f"{k[0]}x{k[1]}": v / 1e9 for k, v in rates.items()},
+                      "measured": len(rates)}
         table[key] = cache[key]
         out.append(best)
     if use_cache:

@@ -63,11 +63,13 @@ def _boundary_mask(nx, ny, nz):
             (k == 0) | (k == nz + 1))
 
 
-def uniform_grid_f64(nx, ny, nz, g=0, px=None):
+def uniform_grid_f64(nx, ny, nz, g=0, px=None, planes=None):
     """Padded FP64 grid (nz+2, ny+2, px): interior U[0,1) (seed 0), boundary layer
-    U[0,1) (seed 1); the row padding beyond nx+2 is zero."""
+    U[0,1) (seed 1); the row padding beyond nx+2 is zero.  ``planes=(lo, hi)``
+    returns only the global planes lo..hi (the same values, drawn by counter)."""
     px = nx + 2 if px is None else px
-    out = np.zeros((nz + 2, ny + 2, px), dtype=np.float64)
+    lo, hi = (0, nz + 1) if planes is None else planes
+    out = np.zeros((hi - lo + 1, ny + 2, px), dtype=np.float64)
     plane = (nx + 2) * (ny + 2)
     j = np.arange(ny + 2, dtype=np.uint64)[:, None]
     i = np.arange(nx + 2, dtype=np.uint64)[None, :]
@@ -75,12 +77,12 @@ def uniform_grid_f64(nx, ny, nz, g=0, px=None):
     jj = np.arange(ny + 2)[:, None]
     ii = np.arange(nx + 2)[None, :]
     edge = (ii == 0) | (ii == nx + 1) | (jj == 0) | (jj == ny + 1)
-    for k in range(nz + 2):
+    for k in range(lo, hi + 1):
         idx = base + np.uint64(plane * k)
         vi = u01(SEED_INTERIOR, g, idx)
         vb = u01(SEED_BOUNDARY, g, idx)
         bnd = edge | (k == 0) | (k == nz + 1)
-        out[k, :, :nx + 2] = np.where(bnd, vb, vi)
+        out[k - lo, :, :nx + 2] = np.where(bnd, vb, vi)
     return out
 
 

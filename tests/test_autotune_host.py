@@ -39,3 +39,28 @@ def test_tune_measures_once_then_uses_cache(tmp_path, monkeypatch):
     calls.clear()
     ts2, _ = autotune.tune(shapes, "f32", candidates=cands, device="cpu")
     assert ts2 == ts and calls == []
+
+
+def test_model_prunes_the_measured_candidates(tmp_path, monkeypatch):
+    """With the model's parameters only the first `keep` candidates in model order
+    are measured, and the best of those is chosen."""
+    from paper_0912_4506_gb300 import autotune, model
+    monkeypatch.setenv("JACOBI_GB300_CACHE", str(tmp_path))
+    monkeypatch.setattr(torch.cuda, "get_device_name", lambda dev=None: "FakeGPU")
+    monkeypatch.setattr(torch.cuda, "get_device_properties",
+                        lambda dev=None: types.SimpleNamespace(multi_processor_count=152))
+    calls = []
+
+    def fake_time(shape, dtype, cand, sweeps, device, reps):
+        calls.append(cand)
+        return 1e9 * (cand[1] + (1 if cand[0] == 64 else 0))
+
+    monkeypatch.setattr(autotune, "_time_shape", fake_time)
+    cands = ((128, 1), (128, 2), (64, 2), (64, 3), (64, 4), (64, 5), (64, 6))
+    params = dict(hbm_gbs=6800.0, sm_mhz=2070.0, sms=152, inst_per_update=17.0)
+    shape = (96, 80, 64)
+    order = model.order_candidates(list(cands), shape, 4, **params)
+    best, _ = autotune.tune([shape], "f32", candidates=cands, device="cpu",
+                            model_params=params, keep=3)
+    assert calls == order[:3]
+    assert best[0] == max(order[:3], key=lambda c: c[1] + (1 if c[0] == 64 else 0))

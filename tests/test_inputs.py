@@ -69,3 +69,14 @@ def test_to_dtype():
     assert np.array_equal(f[:, :, :8], a.astype(np.float32))
     b = inputs.to_dtype(a, "bf16", px=16)
     assert b.dtype == np.uint16 and b.shape == (4, 5, 16)
+
+
+def test_plane_range_equals_slice_of_full_grid():
+    """A rank of the z-slab decomposition draws only its planes: the same values
+    the full grid has there (counter-based generator)."""
+    import numpy as np
+    from paper_0912_4506_gb300 import inputs
+    full = inputs.uniform_grid_f64(11, 7, 20, px=14)
+    for lo, hi in ((0, 4), (3, 12), (15, 21), (0, 21)):
+        part = inputs.uniform_grid_f64(11, 7, 20, px=14, planes=(lo, hi))
+        assert np.array_equal(part, full[lo:hi + 1])

@@ -1,7 +1,8 @@
-"""The multi-rank form of the z-slab decomposition on CPU ranks (gloo): each
-rank owns one slab, exchanges its h+1 halo planes with its neighbours by
-send/recv every h sweeps, sweeps its slab with the CPU oracle, and rank 0
-assembles the cores; the result equals the oracle's single-grid sweep."""
+"""The multi-rank z-slab decomposition (slabs.RankSlab, the class a multi-GPU run
+uses) on CPU ranks over gloo: each rank draws its own planes, exchanges its h+1
+halo planes with its neighbours by send/recv before every pass, sweeps its slab
+with the CPU oracle in place of the library, and rank 0 assembles the cores; the
+result equals the oracle's single-grid sweep."""
 import os
 import socket
 import subprocess
@@ -18,33 +19,19 @@ from paper_0912_4506_gb300 import inputs, slabs
 dist.init_process_group("gloo", init_method="env://")
 r, P = dist.get_rank(), dist.get_world_size()
 nx, ny, nz, h, n = 12, 9, {nz}, {h}, {n}
-a = inputs.uniform_grid_f64(nx, ny, nz)          # every rank draws the same grid
 z0, z1 = slabs.slab_ranges(nz, P)[r]
 lo, hi = slabs.slab_extent(z0, z1, nz, h)
-mine = a[lo:hi + 1].copy()
-plan = slabs.halo_plan(nz, P, h)
-done = 0
-while done < n:
-    d = min(h, n - done)
-    reqs = []
-    for dst, gp, src, k in plan:                  # post sends of my core planes
-        if src == r:
-            buf = torch.from_numpy(np.ascontiguousarray(mine[gp - lo:gp - lo + k]))
-            reqs.append(dist.isend(buf, dst))
-    for dst, gp, src, k in plan:                  # receive my halo planes
-        if dst == r:
-            buf = torch.empty((k, ny + 2, nx + 2), dtype=torch.float64)
-            dist.recv(buf, src)
-            mine[gp - lo:gp - lo + k] = buf.numpy()
-    for q in reqs:
-        q.wait()
-    mine = oracle.sweeps(mine, d, nx=nx)
-    done += d
-core = mine[(z0 if r > 0 else 0) - lo:(z1 if r < P - 1 else nz + 1) - lo + 1]
+# each rank draws only its own planes (the counter-based generator gives the
+# values the single grid has there)
+mine = torch.from_numpy(inputs.uniform_grid_f64(nx, ny, nz, planes=(lo, hi)))
+sweeper = lambda t, d: torch.from_numpy(oracle.sweeps(t.numpy(), d, nx=nx))
+rs = slabs.RankSlab(nx, ny, nz, h, mine, r, P, sweeper=sweeper)
+rs.sweep(n, {t})
 parts = [None] * P
-dist.all_gather_object(parts, (r, core.tolist()))
+dist.all_gather_object(parts, (r, rs.core().numpy().tolist()))
 if r == 0:
     full = np.concatenate([np.array(c) for _, c in sorted(parts, key=lambda x: x[0])])
+    a = inputs.uniform_grid_f64(nx, ny, nz)
     print(json.dumps({{"equal": bool(np.array_equal(full, oracle.sweeps(a, n, nx=nx)))}}))
 dist.destroy_process_group()
 """
@@ -56,10 +43,10 @@ def _port():
         return s.getsockname()[1]
 
 
-def _run(world, nz, h, n):
+def _run(world, nz, h, n, t=None):
     import json
     port = _port()
-    code = _WORKER.format(root=ROOT, nz=nz, h=h, n=n)
+    code = _WORKER.format(root=ROOT, nz=nz, h=h, n=n, t=t)
     procs = []
     for r in range(world):
         env = dict(os.environ, RANK=str(r), WORLD_SIZE=str(world), MASTER_ADDR="127.0.0.1",
@@ -80,3 +67,12 @@ def test_two_ranks_multi_layer_halo():
 
 def test_three_ranks_deep_halo():
     assert _run(3, 24, 5, 12)["equal"]
+
+
+def test_four_ranks_shallower_passes_than_halo():
+    # passes of depth 2 with 4-plane halos: the exchange still happens every pass
+    assert _run(4, 32, 4, 9, t=2)["equal"]
+
+
+def test_single_rank_is_the_plain_sweep():
+    assert _run(1, 10, 3, 7)["equal"]

@@ -13,7 +13,8 @@ the previous step's result; the work per step is identical.
 
 N > 1 (torchrun, one rank per GPU): every rank runs its own grid (replicas,
 weak scaling, no collective on the data path); value = all ranks' lattice-site
-updates / max-over-ranks time.  --impl reference times the CPU oracle (the
+updates / max-over-ranks time.  With --slabs the ranks instead share one grid of
+512 x 512 x 512N cells cut into z-slabs (Sect. 2.1), halos exchanged by NCCL.  --impl reference times the CPU oracle (the
 reference statement of the method) on the host cores on a bounded sample of the
 same workload.
 """
@@ -36,7 +37,10 @@ ALGO_BYTES_PER_LUP = {"f64": 16, "f32": 8, "bf16": 4}
 # kernel on a 384^3 grid (dram__bytes_read.sum + dram__bytes_write.sum), scaled
 # to 512^3 by the lattice-site updates (traffic is proportional to them: 16 B per
 # update, no re-reads).  A kernel without a capture of its current code: None.
-TRAFFIC_PER_LAUNCH = {}
+TRAFFIC_PER_LAUNCH = {
+    # 482.2 MB read + 408.7 MB written for 384^3 (56.6 M updates)
+    "plain_sweep_kernel<F64,emu=8>": round((482179072 + 408687872) * (512 / 384) ** 3),
+}
 
 # Instructions per computed cell update of the blocked kernels, read from ncu
 # captures of the FP32 and bf16 depth-3 kernels at 384^3 (warp instructions per
@@ -46,8 +50,8 @@ TRAFFIC_PER_LAUNCH = {}
 MODEL_INST_PER_UPDATE = {"f32": 17.0, "bf16": 23.4, "f64": 150.0}
 MODEL_FP64_OPS_PER_UPDATE = 2  # the FP64-unit share of an accumulator update
 
-# Pipe-rate probes (jacobi_pipe_probe): launch shape and operations per update of
-# the FP64 sweep with 3 of its 5 additions on the integer pipes.
+# Pipe-rate probes (jacobi_pipe_probe): launch shape, and operations per update of
+# the FP64 sweep with 4 of its 5 additions through the integer-pipe accumulator.
 PROBE_BLOCKS_PER_SM, PROBE_THREADS = 8, 256
 F64_UNIT_OPS_PER_LUP = {"all_fp64": 6, "acc4": 2}   # FP64-unit operations per update
 ACC_ADDS_PER_LUP = 4                                 # additions through the accumulator

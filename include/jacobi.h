@@ -338,7 +338,7 @@ JAC_API const char *jacobi_strerror(int code);
 
 /*
  * jacobi_pipe_probe — measurement kernels for the roofline of the sweeps (no
- * counterpart in the paper; the paper's own model, Sect. 1.3 Eq. 4-5, needs the
+ * counterpart in the paper; the paper's own model, Sect. 1.4 Eq. 4-5, needs the
  * machine's rates as inputs).  Launches `blocks` x `threads` threads (threads a
  * multiple of 32, at most 256), each running JAC_PROBE_CHAINS independent
  * dependency chains of `iters` operations of one kind from registers:

@@ -4,7 +4,7 @@ For every distinct grid shape it times the batched persistent kernel itself on
 enough replicas of that shape to fill the GPU, for each candidate (tile width,
 depth), and keeps the fastest (lattice-site updates per second).  Results are cached in a
 JSON file keyed by device name, dtype and shape, so a batch is tuned once.
-The paper chose its blocking parameters experimentally as well (Sect. 1.4: the
+The paper chose its blocking parameters experimentally as well (Sect. 1.5: the
 parameter space is large and the best values were found by measurement).
 """
 import json

@@ -12,7 +12,7 @@ with ``i`` the cell's linear index in the compact padded layout
 ``i + (nx+2) * (j + (ny+2) * k)`` (independent of any row padding), ``g`` the grid
 number (0 for a single grid).  FP32 values are RN(double), bf16 values RNE(FP32).
 
-Workloads (the paper's synthetic cubic grids, Sect. 1.4 uses 600^3):
+Workloads (the paper's synthetic cubic grids, Sect. 1.5 uses 600^3):
   * uniform grids: interior U[0,1) from seed 0, boundary layer U[0,1) from seed 1;
   * the Laplace problem: boundary data u = x^2 - y^2 + 0.5 z on the padded
     index lattice, interior zero;

@@ -1,5 +1,5 @@
 """Performance model of a temporally-blocked pass: the paper's single-cache model
-(Sect. 1.3, Eq. 4-5) restated for one GB300 and used to order the autotuner's
+(Sect. 1.4, Eq. 4-5) restated for one GB300 and used to order the autotuner's
 candidates.
 
 The paper's Eq. 4 gives the time of t block updates of a thread team as the

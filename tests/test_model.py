@@ -1,4 +1,4 @@
-"""The performance model of a blocked pass (Sect. 1.3, Eq. 4-5 restated for the
+"""The performance model of a blocked pass (Sect. 1.4, Eq. 4-5 restated for the
 GPU), checked against the paper's own numbers and hand-computed tile cases."""
 import math
 
@@ -9,7 +9,7 @@ from paper_0912_4506_gb300 import model
 
 def test_eq5_matches_the_papers_nehalem_prediction():
     """M_s / M_s,1 = 2 and M_c / M_s,1 = 8 give 16T / (7 + 4T) at t = 4, and 1.45
-    for one team (Sect. 1.3); the large-tT limit is M_c / M_s = 4."""
+    for one team (Sect. 1.4); the large-tT limit is M_c / M_s = 4."""
     for T in (1, 2, 3, 5):
         assert model.eq5_speedup(4, 1.0, 2.0, 8.0, teams=T) == pytest.approx(16 * T / (7 + 4 * T))
     assert round(model.eq5_speedup(4, 1.0, 2.0, 8.0), 2) == 1.45

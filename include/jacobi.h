@@ -72,20 +72,22 @@ typedef enum {
 typedef enum {
     JAC_KERNEL_AUTO = 0,   /* planner: plain streaming or temporal blocking        */
     JAC_KERNEL_PLAIN = 1,  /* one sweep per pass over HBM (Eq. 1, 2*elem B/LUP)   */
-    JAC_KERNEL_TB = 2      /* temporally blocked passes of depth t (Sect. 1.3)     */
+    JAC_KERNEL_TB = 2,     /* temporally blocked passes of depth t (Sect. 1.3)     */
+    JAC_KERNEL_WAVE = 3    /* pipelined passes of depth t, no halo recompute
+                              (Sect. 1.3, relaxed synchronisation, Eq. 3)          */
 } jac_kernel;
 
 typedef struct jacobi_s *jacobi_t;
 
 /* Description of the launch sequence a sweep call will use (jacobi_plan). */
 typedef struct {
-    int kernel;            /* JAC_KERNEL_PLAIN or JAC_KERNEL_TB                    */
+    int kernel;            /* JAC_KERNEL_PLAIN, JAC_KERNEL_TB or JAC_KERNEL_WAVE   */
     int t;                 /* depth of the full passes (1 for plain)              */
     int passes;            /* number of kernel launches                           */
     int remainder_t;       /* depth of the last pass (0 if all passes are full)   */
     int tile_x, tile_y;    /* output tile of one CTA (cells)                      */
     int ext_x, ext_y;      /* loaded tile including the t-cell halo              */
-    int kchunk;            /* output k-planes per CTA                             */
+    int kchunk;            /* output k-planes per CTA (pipelined: per work item)   */
     int threads;           /* threads per CTA                                     */
     int smem_bytes;        /* dynamic shared memory per CTA                       */
     int grid_x, grid_y, grid_z;
@@ -109,6 +111,24 @@ JAC_API int jacobi_create(jacobi_t *out, int nx, int ny, int nz, int dtype, void
                   void *grid_b, long long row_pitch, void *stream);
 
 /*
+ * jacobi_create_inplace — bind ONE caller-owned device grid (layout as for
+ * jacobi_create) to a handle whose sweeps update it in place: half the memory of
+ * the two grids A and B, the aim of the paper's compressed grid (Sect. 1.3).  The
+ * paper shifts every result by one cell so that a sequential sweep never
+ * overwrites a value it still needs; here the pipelined passes' counters give the
+ * same guarantee, so values stay where they are.  Sweeps on this handle run the
+ * pipelined kernel only (JAC_KERNEL_AUTO or JAC_KERNEL_WAVE), every pass of depth
+ * >= 2 (the last update of a pass must not overwrite values that the first
+ * update of a neighbouring tile still reads): t == 1, or nsweeps == 1, returns
+ * JAC_EUNSUPPORTED, and a remainder of one sweep is merged into the last pass
+ * (depth t+1).  final_is_b is always 0.  jacobi_sweep_rhs and jacobi_adjoint
+ * return JAC_EUNSUPPORTED; jacobi_download with from_b != 0 returns JAC_EINVAL.
+ * Needs no boundary copy (there is no second grid).
+ */
+JAC_API int jacobi_create_inplace(jacobi_t *out, int nx, int ny, int nz, int dtype, void *grid,
+                          long long row_pitch, void *stream);
+
+/*
  * jacobi_sweep — nsweeps sweeps of Eq. 1, A -> B -> A ... (Sect. 1.1).
  *   t          temporal-blocking depth request (Sect. 1.3): 0 = planner's choice
  *              (FP64: 1, FP32/bf16: 3), 1 = one sweep per pass (FP64: the
@@ -128,7 +148,22 @@ JAC_API int jacobi_sweep(jacobi_t h, int nsweeps, int t, int *final_is_b);
 
 /* jacobi_sweep_ex — as jacobi_sweep, with the kernel family forced
  * (JAC_KERNEL_PLAIN: the register-march streaming kernel for every dtype;
- * JAC_KERNEL_TB with t == 1 runs the blocked kernel at depth 1). */
+ * JAC_KERNEL_TB with t == 1 runs the blocked kernel at depth 1).
+ *
+ * JAC_KERNEL_WAVE: pipelined passes (Sect. 1.3 with the relaxed synchronisation
+ * of Eq. 3).  One persistent launch per pass of depth t (1 <= t <= 32; t == 0:
+ * 2 for FP64, 4 for FP32/bf16).  Each work item is one of the t updates of an
+ * x-y tile over a few planes, and it starts once the items it reads from and
+ * the items that still read the buffer it overwrites are done, as the paper's
+ * per-thread counters pace its team.  Updates 1..t-1 of a pass live in ring
+ * buffers that the handle allocates on first use (kept until destroy, grown when
+ * a deeper pass needs more; sized to stay in L2), so no cell is recomputed and
+ * each pass reads and writes the grid once.  Every wait on another item is
+ * bounded (2 s); a wait that runs out ends the launch, and jacobi_check returns
+ * JAC_ETIMEOUT.  Results are bit-identical to the other kernels.  For failure-
+ * detection tests only, the environment variable
+ * JACOBI_WAVE_TEST_MISSING_PRODUCER=1 withholds the first block of update 1 of
+ * every tile (and shortens the wait limit to 0.1 s), so the call times out. */
 JAC_API int jacobi_sweep_ex(jacobi_t h, int nsweeps, int t, int kernel, int *final_is_b);
 
 /* jacobi_plan — fill *info with the plan jacobi_sweep_ex(h, nsweeps, t, kernel)

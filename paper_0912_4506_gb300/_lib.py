@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(HERE, "libjacobi_gb300.so")
 
 JAC_OK, JAC_EINVAL, JAC_ENOMEM, JAC_ECUDA, JAC_ETIMEOUT, JAC_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 JAC_F64, JAC_F32, JAC_BF16 = 0, 1, 2
-JAC_KERNEL_AUTO, JAC_KERNEL_PLAIN, JAC_KERNEL_TB = 0, 1, 2
+JAC_KERNEL_AUTO, JAC_KERNEL_PLAIN, JAC_KERNEL_TB, JAC_KERNEL_WAVE = 0, 1, 2, 3
 JAC_OP_SWEEP, JAC_OP_RHS, JAC_OP_ADJOINT = 0, 1, 2
 JAC_PROBE_DADD, JAC_PROBE_FADD, JAC_PROBE_LOP3, JAC_PROBE_IMAD, JAC_PROBE_EMU_ADD = 0, 1, 2, 3, 4
 JAC_PROBE_ACC_ADD = 5
@@ -22,7 +22,8 @@ EXPORTS = ["jacobi_create", "jacobi_sweep", "jacobi_sweep_ex", "jacobi_plan",
            "jacobi_strerror", "jacobi_version", "jacobi_sweep_noalloc",
            "jacobi_batch_create", "jacobi_batch_run", "jacobi_batch_info", "jacobi_batch_check",
            "jacobi_batch_destroy", "jacobi_emulated_add", "jacobi_copy_planes",
-           "jacobi_max_depth", "jacobi_pipe_probe", "jacobi_emulated_sum6"]
+           "jacobi_max_depth", "jacobi_pipe_probe", "jacobi_emulated_sum6",
+           "jacobi_create_inplace"]
 
 JAC_BATCH_NO_GRAPH, JAC_BATCH_TEST_MISSING_PRODUCER = 1, 2
 
@@ -59,6 +60,7 @@ def load(path=None):
     PI = ctypes.POINTER(ctypes.c_int)
     sig = {
         "jacobi_create": ([ctypes.POINTER(P), I, I, I, I, P, P, LL, P], I),
+        "jacobi_create_inplace": ([ctypes.POINTER(P), I, I, I, I, P, LL, P], I),
         "jacobi_sweep": ([P, I, I, PI], I),
         "jacobi_sweep_ex": ([P, I, I, I, PI], I),
         "jacobi_plan": ([P, I, I, I, ctypes.POINTER(PlanInfo)], I),
@@ -106,6 +108,13 @@ def jacobi_create(nx, ny, nz, dtype, grid_a, grid_b, row_pitch, stream):
     h = ctypes.c_void_p()
     _ck(load().jacobi_create(ctypes.byref(h), nx, ny, nz, dtype, grid_a, grid_b, row_pitch,
                              stream), "jacobi_create")
+    return h
+
+
+def jacobi_create_inplace(nx, ny, nz, dtype, grid, row_pitch, stream):
+    h = ctypes.c_void_p()
+    _ck(load().jacobi_create_inplace(ctypes.byref(h), nx, ny, nz, dtype, grid, row_pitch,
+                                     stream), "jacobi_create_inplace")
     return h
 
 

@@ -11,7 +11,7 @@ import torch
 
 from . import _lib
 from ._lib import (JAC_BF16, JAC_F32, JAC_F64, JAC_KERNEL_AUTO, JAC_KERNEL_PLAIN,
-                   JAC_KERNEL_TB, JacobiError)
+                   JAC_KERNEL_TB, JAC_KERNEL_WAVE, JacobiError)
 
 _DT = {torch.float64: JAC_F64, torch.float32: JAC_F32, torch.bfloat16: JAC_BF16}
 _NAME = {"f64": torch.float64, "f32": torch.float32, "bf16": torch.bfloat16}
@@ -84,24 +84,34 @@ class Jacobi:
     """A pair of ping-pong grids bound to a library handle.
 
     ``A`` holds the initial grid with its boundary layer; ``B`` (allocated with
-    A's layout if not given) receives A's boundary layer at construction.
+    A's layout if not given) receives A's boundary layer at construction.  With
+    ``inplace=True`` there is no B: the sweeps update A in place (pipelined
+    passes of depth >= 2 only, see jacobi_create_inplace).
     """
 
-    def __init__(self, A, B=None, stream=None):
+    def __init__(self, A, B=None, stream=None, inplace=False):
         """``stream``: the torch stream the handle launches on (default: the
         current stream at construction)."""
         nx, ny, nz, px = grid_geom(A)
         self.nx, self.ny, self.nz, self.px = nx, ny, nz, px
         self.A = A
-        self.B = alloc_like(A) if B is None else B
-        if grid_geom(self.B) != (nx, ny, nz, px) or self.B.dtype != A.dtype:
+        self.inplace = bool(inplace)
+        if self.inplace and B is not None:
+            raise ValueError("an in-place handle has no second grid")
+        self.B = None if self.inplace else (alloc_like(A) if B is None else B)
+        if self.B is not None and (grid_geom(self.B) != (nx, ny, nz, px) or
+                                   self.B.dtype != A.dtype):
             raise ValueError("B must match A (shape, dtype, row pitch)")
         self.dtype = _DT[A.dtype]
         self.device = A.device
         with torch.cuda.device(self.device):
             sp = _stream_ptr(self.device) if stream is None else stream.cuda_stream
-            self._h = _lib.jacobi_create(nx, ny, nz, self.dtype, A.data_ptr(),
-                                         self.B.data_ptr(), px, sp)
+            if self.inplace:
+                self._h = _lib.jacobi_create_inplace(nx, ny, nz, self.dtype, A.data_ptr(),
+                                                     px, sp)
+            else:
+                self._h = _lib.jacobi_create(nx, ny, nz, self.dtype, A.data_ptr(),
+                                             self.B.data_ptr(), px, sp)
 
     # ------------------------------------------------------------------
     def sweep(self, nsweeps, t=0, kernel=JAC_KERNEL_AUTO):

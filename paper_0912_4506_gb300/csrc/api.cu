@@ -15,6 +15,7 @@
 #include "launch.h"
 #include "plan.h"
 #include "tb.cuh"
+#include "wave.cuh"
 
 using namespace jac;
 
@@ -35,6 +36,9 @@ struct jacobi_s {
     int rho_box_x, rho_box_y;
     void* fbuf;           // adjoint: face values per sweep (owned, grown on demand)
     size_t fbuf_bytes;
+    int inplace;          // one grid (jacobi_create_inplace): b == nullptr
+    void* wbuf;           // pipelined passes: rings and counters (owned, grown on demand)
+    size_t wbuf_bytes;
 };
 
 namespace {
@@ -54,11 +58,154 @@ int emu_half_adds(int code) { return code >= 16 ? 2 * ((code - 16) & 7) : code; 
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// Grow the handle's device buffer `*buf` to at least `need` bytes (the stream
+// is drained before an old buffer is released).
+int grow_buffer(jacobi_s* h, void** buf, size_t* bytes, size_t need) {
+    if (need <= *bytes) return JAC_OK;
+    if (*buf) {
+        if (cudaStreamSynchronize(h->stream) != cudaSuccess) return JAC_ECUDA;
+        cudaFree(*buf);
+        *buf = nullptr;
+        *bytes = 0;
+    }
+    if (cudaMalloc(buf, need) != cudaSuccess) {
+        *buf = nullptr;
+        return JAC_ENOMEM;
+    }
+    *bytes = need;
+    return JAC_OK;
+}
+
+// Pipelined (wavefront) passes: t updates per pass with no halo recompute; in
+// place for a one-grid handle (every pass of depth >= 2).
+int run_wave(jacobi_s* h, int nsweeps, int t, int* final_is_b, jacobi_plan_info* info_only) {
+    const WaveEntry* we = wave_for(h->dtype);
+    if (t == 0) t = default_wave_t(h->dtype);
+    if (t > kMaxWaveDepth) return JAC_EUNSUPPORTED;
+    DepthPlan dp{0, 0, 0};
+    if (nsweeps > 0) {
+        dp.t_full = std::min(t, nsweeps);
+        dp.n_full = nsweeps / dp.t_full;
+        dp.t_last = nsweeps % dp.t_full;
+        if (h->inplace) {
+            // an in-place pass needs depth >= 2 (its last level overwrites values
+            // that its first level of the neighbouring tiles still reads otherwise)
+            if (dp.t_full < 2) return JAC_EUNSUPPORTED;
+            if (dp.t_last == 1) {
+                dp.n_full -= 1;
+                dp.t_last = dp.t_full + 1;
+                if (dp.t_last > kMaxWaveDepth) return JAC_EUNSUPPORTED;
+            }
+        }
+    }
+    WavePlan wp[2];
+    size_t need = 0;
+    for (int p = 0; p < 2; ++p) {
+        const int d = p == 0 ? dp.t_full : dp.t_last;
+        if (d == 0 || (p == 0 && dp.n_full == 0)) continue;
+        if (!wave_plan(h->dtype, h->g, d, *we, h->device, h->num_sms, &wp[p]))
+            return JAC_EUNSUPPORTED;
+        const size_t ring = (wp[p].ring_bytes + 255) & ~(size_t)255;
+        need = std::max(need, ring + wp[p].sync_ints * sizeof(int));
+    }
+    if (info_only) {
+        std::memset(info_only, 0, sizeof(*info_only));
+        info_only->kernel = JAC_KERNEL_WAVE;
+        info_only->passes = dp.passes();
+        if (dp.passes() > 0) {
+            const WavePlan& w = dp.n_full > 0 ? wp[0] : wp[1];
+            info_only->t = w.t;
+            info_only->remainder_t = dp.n_full > 0 ? dp.t_last : 0;
+            info_only->tile_x = 32 * we->V;
+            info_only->tile_y = we->WY;
+            info_only->ext_x = 32 * we->V;
+            info_only->ext_y = we->WY;
+            info_only->kchunk = w.kb;
+            info_only->threads = 32 * (we->WY + 1);
+            info_only->grid_x = w.ctas;
+            info_only->grid_y = 1;
+            info_only->grid_z = 1;
+            info_only->emu_adds = emu_half_adds(we->nemu);
+        }
+        return JAC_OK;
+    }
+    if (dp.passes() == 0) {
+        if (final_is_b) *final_is_b = 0;
+        return JAC_OK;
+    }
+    int rc = grow_buffer(h, &h->wbuf, &h->wbuf_bytes, need);
+    if (rc != JAC_OK) return rc;
+    const int* fast = nullptr;
+    if (we->nemu > 0) {
+        fast = h->status + 16;
+        if (launch_range_check(static_cast<const double*>(h->a), h->g, h->status + 16,
+                               h->stream) != cudaSuccess)
+            return JAC_ECUDA;
+    }
+    // failure-detection tests: the items of the first block of level 1 are never
+    // handed out, so the items that need them wait out a short limit and the
+    // launch ends with the timeout status
+    const char* hook = getenv("JACOBI_WAVE_TEST_MISSING_PRODUCER");
+    const bool missing_producer = hook && hook[0] == '1';
+    int cur_b = 0;
+    for (int p = 0; p < dp.passes(); ++p) {
+        const WavePlan& w = p < dp.n_full ? wp[0] : wp[1];
+        const size_t ring = (w.ring_bytes + 255) & ~(size_t)255;
+        int* sync = reinterpret_cast<int*>(static_cast<char*>(h->wbuf) + ring);
+        if (cudaMemsetAsync(sync, 0, w.sync_ints * sizeof(int), h->stream) != cudaSuccess)
+            return JAC_ECUDA;
+        WaveArgs a;
+        a.g = h->g;
+        a.src = cur_b ? h->b : h->a;
+        a.dst = h->inplace ? h->a : (cur_b ? h->a : h->b);
+        a.ring = h->wbuf;
+        a.t = w.t;
+        a.kb = w.kb;
+        a.nb = w.nb;
+        a.R = w.R;
+        a.rp = w.rp;
+        a.ntx = w.ntx;
+        a.nty = w.nty;
+        a.nitems = w.nitems;
+        a.inplace = h->inplace;
+        a.done = sync;
+        a.ticket = sync + (w.sync_ints - 2);
+        a.abort = sync + (w.sync_ints - 1);
+        a.status = h->status;
+        a.fast = fast;
+        a.one = 1u;
+        a.wait_ns = 2000000000ull;
+        if (missing_producer) {
+            const int first = w.ntx * w.nty;  // tickets of items (s = 1, b = 0, *)
+            if (cudaMemcpyAsync(a.ticket, &first, sizeof(int), cudaMemcpyHostToDevice,
+                                h->stream) != cudaSuccess ||
+                cudaStreamSynchronize(h->stream) != cudaSuccess)
+                return JAC_ECUDA;
+            a.wait_ns = 100000000ull;
+        }
+        if (we->launch(a, w.ctas, h->stream) != cudaSuccess) return JAC_ECUDA;
+        if (!h->inplace) cur_b ^= 1;
+    }
+    if (final_is_b) *final_is_b = cur_b;
+    return JAC_OK;
+}
+
 // Run nsweeps of `mode` as a sequence of passes.  kernel: JAC_KERNEL_*.
 int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void* rho,
                void* grad, int* final_is_b, jacobi_plan_info* info_only) {
     if (!h || nsweeps < 0 || t < 0) return JAC_EINVAL;
-    if (kernel < JAC_KERNEL_AUTO || kernel > JAC_KERNEL_TB) return JAC_EINVAL;
+    if (kernel < JAC_KERNEL_AUTO || kernel > JAC_KERNEL_WAVE) return JAC_EINVAL;
+    if (h->inplace) {
+        // one grid: only the pipelined passes update it in place
+        if (mode != MODE_PLAIN || (kernel != JAC_KERNEL_AUTO && kernel != JAC_KERNEL_WAVE))
+            return JAC_EUNSUPPORTED;
+        kernel = JAC_KERNEL_WAVE;
+    }
+    if (kernel == JAC_KERNEL_WAVE) {
+        if (mode != MODE_PLAIN) return JAC_EUNSUPPORTED;
+        if (cudaSetDevice(h->device) != cudaSuccess) return JAC_ECUDA;
+        return run_wave(h, nsweeps, t, final_is_b, info_only);
+    }
     if (t == 0) t = default_t(h->dtype, mode);
     // depth 1: FP64 takes the register-march streaming kernel (FP64-pipe bound, with
     // the integer-pipe additions); FP32/bf16 take the TMA-ring kernel at depth 1
@@ -163,19 +310,8 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
                                      (long long)h->g.nx * h->g.ny);
     if (mode == MODE_ADJ && nsweeps > 0) {
         const size_t need = (size_t)fstride * (size_t)nsweeps * (size_t)elem_size(h->dtype);
-        if (need > h->fbuf_bytes) {
-            if (h->fbuf) {
-                if (cudaStreamSynchronize(h->stream) != cudaSuccess) return JAC_ECUDA;
-                cudaFree(h->fbuf);
-                h->fbuf = nullptr;
-                h->fbuf_bytes = 0;
-            }
-            if (cudaMalloc(&h->fbuf, need) != cudaSuccess) {
-                h->fbuf = nullptr;
-                return JAC_ENOMEM;
-            }
-            h->fbuf_bytes = need;
-        }
+        const int grc = grow_buffer(h, &h->fbuf, &h->fbuf_bytes, need);
+        if (grc != JAC_OK) return grc;
     }
 
     int cur_b = 0;  // 0: current data in A
@@ -234,13 +370,13 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
 
 extern "C" {
 
-int jacobi_create(jacobi_t* out, int nx, int ny, int nz, int dtype, void* grid_a, void* grid_b,
-                  long long row_pitch, void* stream) {
+static int create_handle(jacobi_t* out, int nx, int ny, int nz, int dtype, void* grid_a,
+                         void* grid_b, long long row_pitch, void* stream) {
     if (!out) return JAC_EINVAL;
     *out = nullptr;
     int rc = check_grid_args(nx, ny, nz, dtype, row_pitch);
     if (rc != JAC_OK) return rc;
-    if (!grid_a || !grid_b || grid_a == grid_b || !aligned16(grid_a) || !aligned16(grid_b))
+    if (!grid_a || grid_a == grid_b || !aligned16(grid_a) || (grid_b && !aligned16(grid_b)))
         return JAC_EINVAL;
     jacobi_s* h = new (std::nothrow) jacobi_s();
     if (!h) return JAC_ENOMEM;
@@ -252,6 +388,7 @@ int jacobi_create(jacobi_t* out, int nx, int ny, int nz, int dtype, void* grid_a
     h->g.plane = row_pitch * (long long)(ny + 2);
     h->a = grid_a;
     h->b = grid_b;
+    h->inplace = grid_b == nullptr;
     h->stream = static_cast<cudaStream_t>(stream);
     if (cudaGetDevice(&h->device) != cudaSuccess ||
         cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device) !=
@@ -264,13 +401,27 @@ int jacobi_create(jacobi_t* out, int nx, int ny, int nz, int dtype, void* grid_a
         return JAC_ENOMEM;
     }
     if (cudaMemsetAsync(h->status, 0, 32 * sizeof(int), h->stream) != cudaSuccess ||
-        launch_boundary_copy(dtype, grid_a, grid_b, h->g, h->stream) != cudaSuccess) {
+        (grid_b && launch_boundary_copy(dtype, grid_a, grid_b, h->g, h->stream) != cudaSuccess)) {
         cudaFree(h->status);
         delete h;
         return JAC_ECUDA;
     }
     *out = h;
     return JAC_OK;
+}
+
+int jacobi_create(jacobi_t* out, int nx, int ny, int nz, int dtype, void* grid_a, void* grid_b,
+                  long long row_pitch, void* stream) {
+    if (!grid_b) {
+        if (out) *out = nullptr;
+        return JAC_EINVAL;
+    }
+    return create_handle(out, nx, ny, nz, dtype, grid_a, grid_b, row_pitch, stream);
+}
+
+int jacobi_create_inplace(jacobi_t* out, int nx, int ny, int nz, int dtype, void* grid,
+                          long long row_pitch, void* stream) {
+    return create_handle(out, nx, ny, nz, dtype, grid, nullptr, row_pitch, stream);
 }
 
 int jacobi_sweep(jacobi_t h, int nsweeps, int t, int* final_is_b) {
@@ -327,13 +478,13 @@ int jacobi_upload(jacobi_t h, const void* host) {
     if (cudaSetDevice(h->device) != cudaSuccess) return JAC_ECUDA;
     if (cudaMemcpyAsync(h->a, host, grid_bytes(h), cudaMemcpyHostToDevice, h->stream) !=
             cudaSuccess ||
-        launch_boundary_copy(h->dtype, h->a, h->b, h->g, h->stream) != cudaSuccess)
+        (h->b && launch_boundary_copy(h->dtype, h->a, h->b, h->g, h->stream) != cudaSuccess))
         return JAC_ECUDA;
     return JAC_OK;
 }
 
 int jacobi_download(jacobi_t h, void* host, int from_b) {
-    if (!h || !host) return JAC_EINVAL;
+    if (!h || !host || (from_b && !h->b)) return JAC_EINVAL;
     if (cudaSetDevice(h->device) != cudaSuccess) return JAC_ECUDA;
     if (cudaMemcpyAsync(host, from_b ? h->b : h->a, grid_bytes(h), cudaMemcpyDeviceToHost,
                         h->stream) != cudaSuccess)
@@ -376,6 +527,7 @@ int jacobi_destroy(jacobi_t h) {
     cudaStreamSynchronize(h->stream);
     cudaFree(h->status);
     if (h->fbuf) cudaFree(h->fbuf);
+    if (h->wbuf) cudaFree(h->wbuf);
     delete h;
     return JAC_OK;
 }
@@ -401,6 +553,6 @@ int jacobi_max_depth(int dtype, int op) {
     return max_depth(dtype, mode);
 }
 
-int jacobi_version(void) { return 200; }
+int jacobi_version(void) { return 300; }
 
 }  // extern "C"

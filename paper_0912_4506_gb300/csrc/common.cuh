@@ -177,6 +177,13 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
+// GPU-scope acquire load of a progress counter written by other CTAs.
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
 // Wait for phase `parity` of `bar`, giving up after ~limit_ns of wall time.
 // Returns false on timeout (the caller records it and leaves cleanly).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,

@@ -43,6 +43,19 @@ struct PlainEntry {
     const void* kernel;
 };
 
+struct WaveArgs;
+using WaveLaunchFn = cudaError_t (*)(const WaveArgs& a, int ctas, cudaStream_t st);
+
+// One instantiation of the pipelined (wavefront) kernel: tiles of 32*V x WY cells.
+struct WaveEntry {
+    int dtype;
+    int V;
+    int WY;
+    int nemu;  // FP64: integer-pipe additions code (0: all on the FP64 unit)
+    WaveLaunchFn launch;
+    const void* kernel;
+};
+
 // Tables provided by the per-dtype translation units.
 const TBEntry* tb_entries_f64(int* n);
 const TBEntry* tb_entries_f64_deep(int* n);
@@ -56,6 +69,9 @@ const PlainEntry* plain_entry_f64();
 const PlainEntry* plain_entries_f64(int* n);  // all emulation variants
 const PlainEntry* plain_entry_f32();
 const PlainEntry* plain_entry_bf16();
+const WaveEntry* wave_entry_f64();
+const WaveEntry* wave_entry_f32();
+const WaveEntry* wave_entry_bf16();
 
 // Auxiliary kernels (aux.cu).
 cudaError_t launch_boundary_copy(int dtype, const void* A, void* B, const Geom& g,

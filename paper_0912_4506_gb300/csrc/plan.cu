@@ -257,4 +257,50 @@ int plan_depths(int dtype, int mode, int nsweeps, int t, DepthPlan* out) {
     return JAC_OK;
 }
 
+const WaveEntry* wave_for(int dtype) {
+    return dtype == JAC_F64 ? wave_entry_f64() : dtype == JAC_F32 ? wave_entry_f32()
+                                                                  : wave_entry_bf16();
+}
+
+int default_wave_t(int dtype) { return dtype == JAC_F64 ? 2 : 4; }
+
+bool wave_plan(int dtype, const Geom& g, int t, const WaveEntry& e, int device, int num_sms,
+               WavePlan* out) {
+    WavePlan w{};
+    if (t < 1 || t > kMaxWaveDepth) return false;
+    w.t = t;
+    // FP64: interior-aligned cells 1..; FP32/bf16: vectors from x = 0 (cells 0..nx)
+    const int cells = dtype == JAC_F64 ? g.nx : g.nx + 1;
+    w.ntx = (cells + 32 * e.V - 1) / (32 * e.V);
+    w.nty = (g.ny + e.WY - 1) / e.WY;
+    const size_t plane_bytes = (size_t)g.plane * (size_t)elem_size(dtype);
+    const size_t budget = (size_t)64 << 20;
+    w.R = 4;
+    w.kb = 1;
+    for (int kb = 16; kb >= 1; kb /= 2)
+        if ((size_t)(t - 1) * (size_t)w.R * (size_t)kb * plane_bytes <= budget) {
+            w.kb = kb;
+            break;
+        }
+    if (const char* env = getenv("JACOBI_WAVE")) {
+        int kb = 0, R = 0;
+        if (sscanf(env, "%d,%d", &kb, &R) == 2 && kb >= 1 && kb <= 256 && R >= 3 && R <= 64) {
+            w.kb = kb;
+            w.R = R;
+        }
+    }
+    w.kb = std::min(w.kb, g.nz);
+    w.rp = w.R * w.kb;
+    w.nb = (g.nz + w.kb - 1) / w.kb;
+    const long long nitems = (long long)t * w.nb * w.ntx * w.nty;
+    if (nitems > (1LL << 30)) return false;
+    w.nitems = (int)nitems;
+    const int occ = cached_occupancy(e.kernel, device, 32 * (e.WY + 1), 0, false);
+    w.ctas = (int)std::min<long long>(nitems, (long long)num_sms * occ);
+    w.ring_bytes = (size_t)(t - 1) * (size_t)w.rp * plane_bytes;
+    w.sync_ints = (size_t)t * w.ntx * w.nty + 2;
+    *out = w;
+    return true;
+}
+
 }  // namespace jac

@@ -69,4 +69,21 @@ struct DepthPlan {
 };
 int plan_depths(int dtype, int mode, int nsweeps, int t, DepthPlan* out);
 
+// Pipelined (wavefront) passes.  A pass of depth t keeps levels 1..t-1 in ring
+// buffers of rp = R * kb planes each; kb (planes per work item) is the largest
+// power of two up to 16 whose rings fit the L2 budget (kb = 1 otherwise), R = 4.
+// JACOBI_WAVE="kb,R" overrides both (measurement runs).
+constexpr int kMaxWaveDepth = 32;
+const WaveEntry* wave_for(int dtype);
+struct WavePlan {
+    int t, kb, R, rp, nb, ntx, nty, nitems, ctas;
+    size_t ring_bytes;   // (t-1) * rp planes
+    size_t sync_ints;    // t * ntiles counters, the ticket and the abort flag
+};
+bool wave_plan(int dtype, const Geom& g, int t, const WaveEntry& e, int device, int num_sms,
+               WavePlan* out);
+
+// Default depth of the pipelined passes.
+int default_wave_t(int dtype);
+
 }  // namespace jac

@@ -1,0 +1,584 @@
+// Pipelined temporal blocking across CTAs: the GPU form of the paper's pipelined
+// scheme with relaxed synchronisation (Sect. 1.3, Eq. 3).
+//
+// In the paper a team of threads shares one cache.  Every block of the grid is
+// updated t times in turn, update s by thread s.  Thread s may start its next
+// block when thread s-1 is at least d_l blocks ahead and thread s+1 at most d_u
+// blocks behind (Eq. 3), which one progress counter per thread tells.  Nothing
+// is recomputed: each of the t updates of a block is done once.
+//
+// Here the team is the whole GPU and the shared cache is the L2:
+//  * A work item is one level s (1..t) of one block.  A block is an x-y tile of
+//    32V x WY cells (one warp per row, V cells per lane) and kb planes in z.
+//  * Levels 1..t-1 live in ring buffers of rp planes each (rp = R kb, full planes
+//    in the grid's layout), sized by the planner to stay in L2.  Level 0 is the
+//    source grid.  Level t is the destination grid, or the source itself for
+//    an in-place pass.
+//  * One counter per (level, tile) counts the blocks finished, in z order.  An
+//    item starts when three things hold.  Level s-1 of the 3 x 3 tile
+//    neighbourhood is done through block b+1: the lower distance of Eq. 3.
+//    Level s+1 of the neighbourhood has finished reading ring block b-R, whose
+//    slot this item overwrites: the upper distance of Eq. 3.  For an in-place
+//    pass (s = t), level 1 of the neighbourhood has read every value of the
+//    block that the item overwrites.
+//  * Items are handed out by one atomic ticket in the order (s + b, s, tile).
+//    In that order every item waits only for items with smaller tickets, so a
+//    persistent grid of any size makes progress.  Each wait is bounded in time;
+//    a timeout sets the status word and the abort flag, and every CTA leaves.
+//  * Ring levels carry the boundary layer like the grids do.  A lane stores
+//    every boundary value it loaded (its own non-interior cells, the row above
+//    y = 1 and below y = ny, the x = 0 and x = nx+1 edge cells) to the same
+//    place in the next level.  The boundary planes z = 0 and z = nz+1 of every
+//    level are read from the source grid, whose boundary layer no pass writes.
+//
+// Loads of the levels go through the coherent path (ld.global.ca): the data
+// was written during this launch by other CTAs, and the GPU-scope acquire of
+// the counters makes it visible to every thread of the CTA after the barrier.
+// The arithmetic is Eq. 1 in its operand order, as in every other kernel, so
+// results are bit-identical to a sequential sweep loop.
+#pragma once
+
+#include "common.cuh"
+#include "emusum.cuh"
+
+namespace jac {
+
+struct WaveArgs {
+    Geom g;
+    const void* src;  // level 0
+    void* dst;        // level t (== src for an in-place pass)
+    void* ring;       // levels 1..t-1, rp planes each
+    int t;            // updates per pass
+    int kb;           // planes per block
+    int nb;           // blocks along z
+    int R;            // ring blocks per level (>= 3)
+    int rp;           // ring planes per level (R * kb)
+    int ntx, nty;     // tiles
+    int nitems;       // t * nb * ntx * nty
+    int inplace;
+    int* done;        // [t][ntx * nty] finished blocks per (level, tile)
+    int* ticket;      // next work item
+    int* abort;       // set by a wait that ran out
+    int* status;      // handle status word (kStatusTimeout)
+    const int* fast;  // FP64: the range flag of the integer-pipe additions
+    uint32_t one;
+    unsigned long long wait_ns;
+};
+
+// The plane sequence of the level read (s-1) and the level written (s).
+template <class S>
+struct WaveLevels {
+    const S* sgrid;  // level 0, and the boundary planes of every level
+    const S* sring;  // ring of level s-1 (s >= 2)
+    S* dgrid;        // destination grid (s == t)
+    S* dring;        // ring of level s (s < t)
+    long long plane;
+    int rp, nz;
+    bool s_in_ring, d_in_ring;
+    __device__ __forceinline__ const S* src(int k, int sl) const {
+        return (s_in_ring && k >= 1 && k <= nz) ? sring + (long long)sl * plane
+                                                 : sgrid + (long long)k * plane;
+    }
+    __device__ __forceinline__ S* dst(int k, int sl) const {
+        return d_in_ring ? dring + (long long)sl * plane : dgrid + (long long)k * plane;
+    }
+    __device__ __forceinline__ int next(int sl) const { return sl + 1 == rp ? 0 : sl + 1; }
+    __device__ __forceinline__ int prev(int sl) const { return sl == 0 ? rp - 1 : sl - 1; }
+};
+
+// Coherent loads (weak ld.global.ca): never the read-only path, whose cache is
+// not kept coherent with stores made during the launch.
+template <class S, int V>
+__device__ __forceinline__ Vec<S, V> ldca_vec(const S* p) {
+    using R = typename RawOf<sizeof(Vec<S, V>)>::T;
+    const R r = __ldca(reinterpret_cast<const R*>(p));
+    Vec<S, V> out;
+    memcpy(&out, &r, sizeof(out));
+    return out;
+}
+
+// One level of one block, FP32/bf16 storage (16-byte vectors of V cells, x
+// origin 0).  The loads of the next step (plane k+2, the rows and edge cells of
+// plane k+1) are issued before the arithmetic of step k.
+template <class Tr, int V>
+__device__ __forceinline__ void wave_march_vec(const WaveLevels<typename Tr::S>& L,
+                                               const Geom& g, int k0, int k1, int x0, int y,
+                                               int lane, bool loadable,
+                                               const bool (&interior)[V], bool all_interior,
+                                               bool left_ok, bool right_ok, long long row) {
+    using S = typename Tr::S;
+    using C = typename Tr::C;
+    using VS = Vec<S, V>;
+    const unsigned FULL = 0xffffffffu;
+    const C c6 = Tr::sixth();
+    const long long px = g.px;
+    const bool el_ok = lane == 0 && left_ok, er_ok = lane == 31 && right_ok;
+    const bool to_ring = L.d_in_ring;
+    const bool row_lo = to_ring && loadable && y == 1;
+    const bool row_hi = to_ring && loadable && y == g.ny;
+    const bool edge_lo = to_ring && el_ok && x0 == 1;          // cell x = 0
+    const bool edge_hi = to_ring && er_ok && x0 + V == g.nx + 1;  // cell x = nx+1
+    VS zero;
+#pragma unroll
+    for (int e = 0; e < V; ++e) zero.v[e] = S(0);
+    auto ldv = [&](const S* p, bool ok) -> VS { return ok ? ldca_vec<S, V>(p) : zero; };
+    auto lds = [&](const S* p, bool ok) -> S { return ok ? __ldca(p) : S(0); };
+
+    int sl = (k0 - 1) % L.rp;  // ring slot of plane k
+    int sln = L.next(sl);      // of plane k+1
+    VS dn = ldv(L.src(k0 - 1, L.prev(sl)) + row, loadable);
+    const S* pc = L.src(k0, sl) + row;
+    VS ct = ldv(pc, loadable);
+    VS no = ldv(pc - px, loadable);
+    VS so = ldv(pc + px, loadable);
+    S el = lds(pc - 1, el_ok), er = lds(pc + V, er_ok);
+    const S* pn = L.src(k0 + 1, sln) + row;  // plane k+1
+    VS up = ldv(pn, loadable);
+
+#pragma unroll 1
+    for (int k = k0; k <= k1; ++k) {
+        const bool more = k < k1;  // planes k+1 <= nz and k+2 <= nz+1 exist
+        const int sl2 = L.next(sln);
+        const S* pn2 = L.src(k + 2, sl2) + row;
+        const VS up2 = ldv(pn2, more && loadable);
+        const VS no2 = ldv(pn - px, more && loadable);
+        const VS so2 = ldv(pn + px, more && loadable);
+        const S el2 = lds(pn - 1, more && el_ok);
+        const S er2 = lds(pn + V, more && er_ok);
+
+        C left = __shfl_up_sync(FULL, Tr::ld(ct.v[V - 1]), 1);
+        C right = __shfl_down_sync(FULL, Tr::ld(ct.v[0]), 1);
+        if (lane == 0) left = Tr::ld(el);
+        if (lane == 31) right = Tr::ld(er);
+        VS outv;
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            const C l = (e == 0) ? left : Tr::ld(ct.v[e - 1]);
+            const C r = (e == V - 1) ? right : Tr::ld(ct.v[e + 1]);
+            C s = Tr::add(l, r);
+            s = Tr::add(s, Tr::ld(no.v[e]));
+            s = Tr::add(s, Tr::ld(so.v[e]));
+            s = Tr::add(s, Tr::ld(dn.v[e]));
+            s = Tr::add(s, Tr::ld(up.v[e]));
+            outv.v[e] = interior[e] ? Tr::st(Tr::mul(s, c6)) : ct.v[e];
+        }
+        S* pd = L.dst(k, sl) + row;
+        if (to_ring) {
+            // the whole vector: computed cells and the boundary values passed on
+            if (loadable) *reinterpret_cast<VS*>(pd) = outv;
+            if (row_lo) *reinterpret_cast<VS*>(pd - px) = no;
+            if (row_hi) *reinterpret_cast<VS*>(pd + px) = so;
+            if (edge_lo) pd[-1] = el;
+            if (edge_hi) pd[V] = er;
+        } else if (all_interior) {
+            *reinterpret_cast<VS*>(pd) = outv;
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                if (interior[e]) pd[e] = outv.v[e];
+        }
+        dn = ct;
+        ct = up;
+        up = up2;
+        no = no2;
+        so = so2;
+        el = el2;
+        er = er2;
+        pn = pn2;
+        sl = sln;
+        sln = sl2;
+    }
+}
+
+// One level of one block, FP64 (interior-aligned cells x0 = 1 + V lane, loaded
+// cell by cell).  K > 0: the first K additions of every update go through the
+// exact unpacked accumulator of emusum.cuh in word form F, with the same warp-vote
+// fallback to the FP64 unit as the streaming sweep; K == 0: all on the FP64 unit.
+template <class Tr, int V, int K, int F>
+__device__ __forceinline__ void wave_march_f64(const WaveLevels<double>& L, const Geom& g,
+                                               int k0, int k1, int x0, int y, int lane,
+                                               const bool (&interior)[V], bool left_ok,
+                                               bool right_ok, long long row, uint32_t one) {
+    static_assert(K >= 0 && K <= 5, "0..5 additions on the integer pipes");
+    const unsigned FULL = 0xffffffffu;
+    const double c6 = Tr::sixth();
+    const long long px = g.px;
+    const bool to_ring = L.d_in_ring;
+    bool okl[V];
+#pragma unroll
+    for (int e = 0; e < V; ++e) okl[e] = (x0 + e) < g.px;
+    auto load = [&](const double* p, double (&out)[V]) {
+#pragma unroll
+        for (int e = 0; e < V; ++e) out[e] = okl[e] ? __ldca(p + e) : 0.0;
+    };
+    const bool row_lo = to_ring && y == 1, row_hi = to_ring && y == g.ny;
+    const bool edge_lo = to_ring && lane == 0 && left_ok && x0 == 1;
+    const bool edge_hi = to_ring && lane == 31 && right_ok && x0 + V == g.nx + 1;
+
+    int sl = (k0 - 1) % L.rp;
+    double dn[V], ct[V], up[V], no[V], so[V];
+    load(L.src(k0 - 1, L.prev(sl)) + row, dn);
+    load(L.src(k0, sl) + row, ct);
+#pragma unroll 1
+    for (int k = k0; k <= k1; ++k) {
+        const int sln = L.next(sl);
+        const double* pc = L.src(k, sl) + row;
+        load(L.src(k + 1, sln) + row, up);
+        load(pc - px, no);
+        load(pc + px, so);
+        double left = __shfl_up_sync(FULL, ct[V - 1], 1);
+        double right = __shfl_down_sync(FULL, ct[0], 1);
+        if (lane == 0) left = left_ok ? __ldca(pc - 1) : 0.0;
+        if (lane == 31) right = right_ok ? __ldca(pc + V) : 0.0;
+        double x[V][6];
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            x[e][0] = (e == 0) ? left : ct[e - 1];
+            x[e][1] = (e == V - 1) ? right : ct[e + 1];
+            x[e][2] = no[e];
+            x[e][3] = so[e];
+            x[e][4] = dn[e];
+            x[e][5] = up[e];
+        }
+        double s[V];
+        if constexpr (K > 0) {
+            const emusum::Mul km = emusum::make_mul(one);
+            emusum::Words acc[V];
+            uint32_t bad = 0;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                acc[e] = emusum::first_w<F>(emusum::unpack_w(x[e][0], km),
+                                            emusum::unpack_w(x[e][1], km), km);
+#pragma unroll
+                for (int i = 2; i <= K; ++i)
+                    emusum::add_w<F>(acc[e], emusum::unpack_w(x[e][i], km), km);
+                if (interior[e]) bad |= acc[e].bad;  // outside cells are not stored
+            }
+            if (__any_sync(FULL, bad != 0u)) {
+#pragma unroll
+                for (int e = 0; e < V; ++e) {
+                    s[e] = __dadd_rn(x[e][0], x[e][1]);
+#pragma unroll
+                    for (int i = 2; i <= K; ++i) s[e] = __dadd_rn(s[e], x[e][i]);
+                }
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e) s[e] = emusum::pack_w(acc[e], km);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e) s[e] = __dadd_rn(x[e][0], x[e][1]);
+        }
+        constexpr int kFirstUnit = K > 0 ? K + 1 : 2;
+        double* pd = L.dst(k, sl) + row;
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+#pragma unroll
+            for (int i = kFirstUnit; i <= 5; ++i) s[e] = __dadd_rn(s[e], x[e][i]);
+            if (interior[e])
+                pd[e] = __dmul_rn(s[e], c6);
+            else if (to_ring && okl[e])
+                pd[e] = ct[e];  // boundary value passed on
+        }
+        if (row_lo) {
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                if (okl[e]) pd[e - px] = no[e];
+        }
+        if (row_hi) {
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                if (okl[e]) pd[e + px] = so[e];
+        }
+        if (edge_lo) pd[-1] = left;
+        if (edge_hi) pd[V] = right;
+#pragma unroll
+        for (int e = 0; e < V; ++e) {
+            dn[e] = ct[e];
+            ct[e] = up[e];
+        }
+        sl = sln;
+    }
+}
+
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Record a wait that ran out: the status word and the abort flag that ends
+// every CTA's loop.
+__device__ __forceinline__ void wave_fail(const WaveArgs& a) {
+    atomicOr(a.status, kStatusTimeout);
+    atomicExch(a.abort, 1);
+}
+
+// The start conditions of item (s, b, tile), watched by the control warp: lane
+// 9c + n watches condition c (0: level s-1 through block b+1; 1: level s+1
+// through block b-R+1, the readers of the ring slot overwritten; 2: level 1
+// through block b+1, in place) of neighbour n of the 3 x 3 tiles.  poll() reads
+// every counter once with relaxed loads; after it succeeds, one fence makes the
+// observation an acquire.
+struct WaveDeps {
+    const int* ptr;
+    int target;
+    __device__ __forceinline__ void init(const WaveArgs& a, int s, int b, int tile, int lane) {
+        const int ntiles = a.ntx * a.nty;
+        ptr = nullptr;
+        target = 0;
+        if (lane < 27) {
+            const int c = lane / 9, nn = lane % 9;
+            const int x = tile % a.ntx + nn % 3 - 1, y = tile / a.ntx + nn / 3 - 1;
+            if (x >= 0 && x < a.ntx && y >= 0 && y < a.nty) {
+                const int n = y * a.ntx + x;
+                if (c == 0 && s >= 2) {
+                    ptr = a.done + (s - 2) * ntiles + n;
+                    target = min(b + 2, a.nb);
+                } else if (c == 1 && s < a.t && b >= a.R) {
+                    ptr = a.done + s * ntiles + n;
+                    target = min(b - a.R + 2, a.nb);
+                } else if (c == 2 && s == a.t && a.inplace) {
+                    ptr = a.done + n;
+                    target = min(b + 2, a.nb);
+                }
+            }
+        }
+    }
+    __device__ __forceinline__ bool poll() const {
+        const bool ok = ptr == nullptr || ld_relaxed(ptr) >= target;
+        return __all_sync(0xffffffffu, ok);
+    }
+};
+
+// Bounded wait of one thread for *c >= target (relaxed polling, then a fence).
+__device__ __forceinline__ bool wave_wait(const int* c, int target, const WaveArgs& a) {
+    if (ld_relaxed(c) < target) {
+        const uint64_t t0 = global_ns();
+        while (ld_relaxed(c) < target) {
+            if (ld_relaxed(a.abort) != 0) return false;
+            if (global_ns() - t0 > a.wait_ns) {
+                wave_fail(a);
+                return false;
+            }
+            __nanosleep(32);
+        }
+    }
+    __threadfence();
+    return true;
+}
+
+// NEMU (FP64): 0 = every addition on the FP64 unit; kAccBaseWave + K + 8F = K
+// additions through the accumulator in word form F (when the range flag is set).
+constexpr int kAccBaseWave = 16;
+
+template <class Tr, int V, int WY, int NEMU>
+__device__ __forceinline__ void wave_item(const WaveArgs& a, int s, int b, int tile, bool fast) {
+    using S = typename Tr::S;
+    constexpr bool kF64 = sizeof(S) == 8;
+    constexpr int XOFF = kF64 ? 1 : 0;
+    const Geom& g = a.g;
+    const int lane = threadIdx.x;
+    const int tx = tile % a.ntx, ty = tile / a.ntx;
+    const int x0 = XOFF + (tx * 32 + lane) * V;
+    const int y = 1 + ty * WY + (int)threadIdx.y;
+    if (y > g.ny) return;  // uniform over the warp
+    const int k0 = 1 + b * a.kb;
+    const int k1 = min(g.nz, k0 + a.kb - 1);
+
+    WaveLevels<S> L;
+    L.plane = g.plane;
+    L.rp = a.rp;
+    L.nz = g.nz;
+    L.sgrid = static_cast<const S*>(a.src);
+    L.s_in_ring = s >= 2;
+    L.sring = static_cast<const S*>(a.ring) + (long long)max(s - 2, 0) * a.rp * g.plane;
+    L.d_in_ring = s < a.t;
+    L.dgrid = static_cast<S*>(a.dst);
+    L.dring = static_cast<S*>(a.ring) + (long long)max(s - 1, 0) * a.rp * g.plane;
+
+    const bool loadable = (x0 + V) <= g.px;
+    bool interior[V];
+    bool all_interior = true;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        interior[e] = (kF64 || loadable) && (x0 + e >= 1) && (x0 + e <= g.nx);
+        all_interior = all_interior && interior[e];
+    }
+    const bool left_ok = x0 >= 1;
+    const bool right_ok = (x0 + V) < g.px;
+    const long long row = g.lin(x0 < g.px ? x0 : 0, y, 0);
+    if constexpr (kF64) {
+        constexpr int K = NEMU >= kAccBaseWave ? ((NEMU - kAccBaseWave) & 7) : 0;
+        constexpr int F = NEMU >= kAccBaseWave ? (((NEMU - kAccBaseWave) / 8) & 3) : 0;
+        if (K > 0 && fast)
+            wave_march_f64<Tr, V, K, F>(L, g, k0, k1, x0, y, lane, interior, left_ok, right_ok,
+                                        row, a.one);
+        else
+            wave_march_f64<Tr, V, 0, 0>(L, g, k0, k1, x0, y, lane, interior, left_ok,
+                                        right_ok, row, a.one);
+    } else {
+        wave_march_vec<Tr, V>(L, g, k0, k1, x0, y, lane, loadable, interior, all_interior,
+                              left_ok, right_ok, row);
+    }
+}
+
+// Named barriers: "job i published" from the control warp to the compute warps,
+// one per job parity so that consecutive jobs never share a barrier generation.
+// (Barrier numbers are immediates, so only barriers 0..2 are allocated.)
+template <int ID, int N>
+__device__ __forceinline__ void named_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(N) : "memory");
+}
+template <int ID, int N>
+__device__ __forceinline__ void named_arrive() {
+    asm volatile("bar.arrive %0, %1;" ::"n"(ID), "n"(N) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void ready_sync(int i) {
+    if (i & 1) named_sync<2, N>(); else named_sync<1, N>();
+}
+template <int N>
+__device__ __forceinline__ void ready_arrive(int i) {
+    if (i & 1) named_arrive<2, N>(); else named_arrive<1, N>();
+}
+
+// "job i computed": an mbarrier with one arrival per compute warp; phase i
+// completes when job i is done.  Non-blocking test, so that the control warp
+// can watch it while it polls the counters of the next job.
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Persistent kernel: each CTA takes tickets until the pass is done.  Warps
+// 0..WY-1 compute; warp WY is the control warp.  For job i the control warp
+// decodes the ticket and polls the job's start conditions; meanwhile it watches
+// job i-1 (still being computed) and releases it as soon as it is done, because
+// job i may depend on it.  Job i is published once its conditions hold and job
+// i-1 is done; if job i-1 is not yet released then, it is released right after.
+// So the checks of job i overlap the arithmetic of job i-1.  A CTA holds at most
+// two unreleased tickets and every wait is on a smaller ticket: the pass makes
+// progress for any number of CTAs.
+template <class Tr, int V, int WY, int NEMU, int MINB>
+__global__ void __launch_bounds__(32 * (WY + 1), MINB) wave_kernel(const WaveArgs a) {
+    const unsigned FULL = 0xffffffffu;
+    constexpr int kThreads = 32 * (WY + 1);
+    __shared__ int s_job[2][4];  // s, b, tile, go
+    __shared__ __align__(8) uint64_t s_done;
+    const int lane = threadIdx.x;
+    const int ntiles = a.ntx * a.nty;
+    if (threadIdx.y == WY && lane == 0) {
+        mbar_init(&s_done, WY);
+        fence_mbar_init();
+    }
+    __syncthreads();
+
+    if (threadIdx.y == WY) {
+        // ---- control warp
+        int d = 1, base = 0;  // lane 0: diagonal s + b of the ticket, its first ticket
+        int it = 0;
+        if (lane == 0) it = atomicAdd(a.ticket, 1);
+        int prev_s = 0, prev_b = 0, prev_tile = 0;
+        auto release = [&](int s, int b, int tile) {
+            if (lane == 0) {
+                int* c = a.done + (s - 1) * ntiles + tile;
+                __threadfence();
+                if (wave_wait(c, b, a)) atomicAdd(c, 1);
+            }
+            __syncwarp();
+        };
+#pragma unroll 1
+        for (int i = 0;; ++i) {
+            int s = 0, b = 0, tile = 0;
+            if (lane == 0 && it < a.nitems) {
+                while (true) {
+                    const int lo = max(1, d - a.nb + 1), hi = min(a.t, d);
+                    const int cnt = (hi - lo + 1) * ntiles;
+                    if (it < base + cnt) {
+                        s = lo + (it - base) / ntiles;
+                        tile = (it - base) % ntiles;
+                        break;
+                    }
+                    base += cnt;
+                    ++d;
+                }
+                b = d - s;
+            }
+            const bool valid = __shfl_sync(FULL, it, 0) < a.nitems;
+            s = __shfl_sync(FULL, s, 0);
+            b = __shfl_sync(FULL, b, 0);
+            tile = __shfl_sync(FULL, tile, 0);
+            WaveDeps deps;
+            deps.init(a, s, b, tile, lane);
+            bool deps_ok = !valid, prev_done = i == 0, prev_released = i == 0, failed = false;
+            const uint64_t t0 = lane == 0 ? global_ns() : 0;
+#pragma unroll 1
+            while (true) {
+                if (!prev_done) prev_done = mbar_test(&s_done, (uint32_t)((i - 1) & 1));
+                if (!deps_ok) deps_ok = deps.poll();
+                if (prev_done && deps_ok) break;
+                if (prev_done && !prev_released) {
+                    release(prev_s, prev_b, prev_tile);
+                    prev_released = true;
+                    continue;
+                }
+                int fail = 0;
+                if (lane == 0) {
+                    if (ld_relaxed(a.abort) != 0) {
+                        fail = 1;
+                    } else if (global_ns() - t0 > a.wait_ns) {
+                        wave_fail(a);
+                        fail = 1;
+                    }
+                }
+                if (__shfl_sync(FULL, fail, 0)) {
+                    failed = true;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            if (!failed && valid) __threadfence();  // acquire side of the counter polls
+            const int go = (valid && !failed && ld_relaxed(a.abort) == 0) ? 1 : 0;
+            if (lane == 0) {
+                s_job[i & 1][0] = s;
+                s_job[i & 1][1] = b;
+                s_job[i & 1][2] = tile;
+                s_job[i & 1][3] = go;
+                if (go) it = atomicAdd(a.ticket, 1);
+            }
+            __syncwarp();
+            ready_arrive<kThreads>(i);
+            if (!prev_released && !failed) release(prev_s, prev_b, prev_tile);
+            if (!go) break;
+            prev_s = s;
+            prev_b = b;
+            prev_tile = tile;
+        }
+        return;
+    }
+
+    // ---- compute warps
+    const bool fast = a.fast != nullptr && *a.fast != 0;
+#pragma unroll 1
+    for (int i = 0;; ++i) {
+        ready_sync<kThreads>(i);
+        if (!s_job[i & 1][3]) break;
+        const int s = s_job[i & 1][0], b = s_job[i & 1][1], tile = s_job[i & 1][2];
+        wave_item<Tr, V, WY, NEMU>(a, s, b, tile, fast);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s_done);
+    }
+}
+
+}  // namespace jac

@@ -163,6 +163,7 @@ int run_wave(jacobi_s* h, int nsweeps, int t, int* final_is_b, jacobi_plan_info*
         a.kb = w.kb;
         a.nb = w.nb;
         a.R = w.R;
+        a.sk = w.sk;
         a.rp = w.rp;
         a.ntx = w.ntx;
         a.nty = w.nty;

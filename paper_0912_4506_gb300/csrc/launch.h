@@ -69,9 +69,9 @@ const PlainEntry* plain_entry_f64();
 const PlainEntry* plain_entries_f64(int* n);  // all emulation variants
 const PlainEntry* plain_entry_f32();
 const PlainEntry* plain_entry_bf16();
-const WaveEntry* wave_entry_f64();
-const WaveEntry* wave_entry_f32();
-const WaveEntry* wave_entry_bf16();
+const WaveEntry* wave_entries_f64(int* n);
+const WaveEntry* wave_entries_f32(int* n);
+const WaveEntry* wave_entries_bf16(int* n);
 
 // Auxiliary kernels (aux.cu).
 cudaError_t launch_boundary_copy(int dtype, const void* A, void* B, const Geom& g,

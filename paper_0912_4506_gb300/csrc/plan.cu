@@ -258,8 +258,13 @@ int plan_depths(int dtype, int mode, int nsweeps, int t, DepthPlan* out) {
 }
 
 const WaveEntry* wave_for(int dtype) {
-    return dtype == JAC_F64 ? wave_entry_f64() : dtype == JAC_F32 ? wave_entry_f32()
-                                                                  : wave_entry_bf16();
+    int n = 0;
+    const WaveEntry* tab = dtype == JAC_F64   ? wave_entries_f64(&n)
+                           : dtype == JAC_F32 ? wave_entries_f32(&n)
+                                              : wave_entries_bf16(&n);
+    int i = 0;
+    if (const char* env = getenv("JACOBI_WAVE_VARIANT")) i = atoi(env);
+    return (i >= 0 && i < n) ? &tab[i] : &tab[0];
 }
 
 int default_wave_t(int dtype) { return dtype == JAC_F64 ? 2 : 4; }
@@ -274,19 +279,25 @@ bool wave_plan(int dtype, const Geom& g, int t, const WaveEntry& e, int device, 
     w.ntx = (cells + 32 * e.V - 1) / (32 * e.V);
     w.nty = (g.ny + e.WY - 1) / e.WY;
     const size_t plane_bytes = (size_t)g.plane * (size_t)elem_size(dtype);
-    const size_t budget = (size_t)64 << 20;
+    const size_t budget = (size_t)256 << 20;
     w.R = 4;
+    w.sk = 2;
     w.kb = 1;
-    for (int kb = 16; kb >= 1; kb /= 2)
+    for (int kb = 32; kb >= 1; kb /= 2)
         if ((size_t)(t - 1) * (size_t)w.R * (size_t)kb * plane_bytes <= budget) {
             w.kb = kb;
             break;
         }
     if (const char* env = getenv("JACOBI_WAVE")) {
-        int kb = 0, R = 0;
-        if (sscanf(env, "%d,%d", &kb, &R) == 2 && kb >= 1 && kb <= 256 && R >= 3 && R <= 64) {
-            w.kb = kb;
-            w.R = R;
+        int kb = 0, R = 0, sk = 0;
+        const int n = sscanf(env, "%d,%d,%d", &kb, &R, &sk);
+        if (n >= 2 && kb >= 1 && kb <= 256 && R >= 3 && R <= 64) {
+            if (n < 3) sk = std::min(2, R - 2);
+            if (sk >= 1 && sk < R - 1) {
+                w.kb = kb;
+                w.R = R;
+                w.sk = sk;
+            }
         }
     }
     w.kb = std::min(w.kb, g.nz);

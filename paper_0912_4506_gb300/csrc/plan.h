@@ -71,12 +71,15 @@ int plan_depths(int dtype, int mode, int nsweeps, int t, DepthPlan* out);
 
 // Pipelined (wavefront) passes.  A pass of depth t keeps levels 1..t-1 in ring
 // buffers of rp = R * kb planes each; kb (planes per work item) is the largest
-// power of two up to 16 whose rings fit the L2 budget (kb = 1 otherwise), R = 4.
-// JACOBI_WAVE="kb,R" overrides both (measurement runs).
+// power of two up to 32 whose rings fit the L2 budget (kb = 1 otherwise), R = 4,
+// ticket skew sk = 2.  JACOBI_WAVE="kb,R" or "kb,R,sk" overrides them
+// (measurement runs); sk defaults to min(2, R - 2) and must stay below R - 1.
 constexpr int kMaxWaveDepth = 32;
+// The pipelined kernel of a dtype (JACOBI_WAVE_VARIANT=i selects alternate i of
+// its table, for measurement runs).
 const WaveEntry* wave_for(int dtype);
 struct WavePlan {
-    int t, kb, R, rp, nb, ntx, nty, nitems, ctas;
+    int t, kb, R, sk, rp, nb, ntx, nty, nitems, ctas;
     size_t ring_bytes;   // (t-1) * rp planes
     size_t sync_ints;    // t * ntiles counters, the ticket and the abort flag
 };

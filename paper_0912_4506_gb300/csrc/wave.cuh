@@ -21,10 +21,15 @@
 //    slot this item overwrites: the upper distance of Eq. 3.  For an in-place
 //    pass (s = t), level 1 of the neighbourhood has read every value of the
 //    block that the item overwrites.
-//  * Items are handed out by one atomic ticket in the order (s + b, s, tile).
-//    In that order every item waits only for items with smaller tickets, so a
-//    persistent grid of any size makes progress.  Each wait is bounded in time;
-//    a timeout sets the status word and the abort flag, and every CTA leaves.
+//  * Items are handed out by one atomic ticket in the order (b + sk s, s, tile)
+//    with a skew sk >= 1 and R > sk + 1.  In that order every item waits only
+//    for items with smaller tickets (its input, level s-1 of block b+1, comes
+//    sk - 1 diagonals earlier; the readers of its ring slot R - sk - 1
+//    diagonals earlier; in place, level 1 of block b+1 earlier for t >= 2), so
+//    a persistent grid of any size makes progress, and with sk = 2 an item's
+//    input was handed out a whole diagonal of items before it.  Each wait is
+//    bounded in time; a timeout sets the status word and the abort flag, and
+//    every CTA leaves.
 //  * Ring levels carry the boundary layer like the grids do.  A lane stores
 //    every boundary value it loaded (its own non-interior cells, the row above
 //    y = 1 and below y = ny, the x = 0 and x = nx+1 edge cells) to the same
@@ -51,7 +56,8 @@ struct WaveArgs {
     int t;            // updates per pass
     int kb;           // planes per block
     int nb;           // blocks along z
-    int R;            // ring blocks per level (>= 3)
+    int R;            // ring blocks per level (> sk + 1)
+    int sk;           // skew of the ticket order
     int rp;           // ring planes per level (R * kb)
     int ntx, nty;     // tiles
     int nitems;       // t * nb * ntx * nty
@@ -99,7 +105,9 @@ __device__ __forceinline__ Vec<S, V> ldca_vec(const S* p) {
 
 // One level of one block, FP32/bf16 storage (16-byte vectors of V cells, x
 // origin 0).  The loads of the next step (plane k+2, the rows and edge cells of
-// plane k+1) are issued before the arithmetic of step k.
+// plane k+1) are issued before the arithmetic of step k.  (Loading two steps
+// ahead, with the registers that takes, measured slower: the march is bound by
+// its resident warps, not by the depth of its loads.)
 template <class Tr, int V>
 __device__ __forceinline__ void wave_march_vec(const WaveLevels<typename Tr::S>& L,
                                                const Geom& g, int k0, int k1, int x0, int y,
@@ -486,7 +494,7 @@ __global__ void __launch_bounds__(32 * (WY + 1), MINB) wave_kernel(const WaveArg
 
     if (threadIdx.y == WY) {
         // ---- control warp
-        int d = 1, base = 0;  // lane 0: diagonal s + b of the ticket, its first ticket
+        int d = 1, base = 0;  // lane 0: diagonal b + sk s of the ticket, its first ticket
         int it = 0;
         if (lane == 0) it = atomicAdd(a.ticket, 1);
         int prev_s = 0, prev_b = 0, prev_tile = 0;
@@ -503,8 +511,11 @@ __global__ void __launch_bounds__(32 * (WY + 1), MINB) wave_kernel(const WaveArg
             int s = 0, b = 0, tile = 0;
             if (lane == 0 && it < a.nitems) {
                 while (true) {
-                    const int lo = max(1, d - a.nb + 1), hi = min(a.t, d);
-                    const int cnt = (hi - lo + 1) * ntiles;
+                    // levels s of diagonal d: b = d - sk s in [0, nb)
+                    const int over = d - (a.nb - 1);
+                    const int lo = over <= 0 ? 1 : max(1, (over + a.sk - 1) / a.sk);
+                    const int hi = min(a.t, d / a.sk);
+                    const int cnt = hi >= lo ? (hi - lo + 1) * ntiles : 0;
                     if (it < base + cnt) {
                         s = lo + (it - base) / ntiles;
                         tile = (it - base) % ntiles;
@@ -513,7 +524,7 @@ __global__ void __launch_bounds__(32 * (WY + 1), MINB) wave_kernel(const WaveArg
                     base += cnt;
                     ++d;
                 }
-                b = d - s;
+                b = d - a.sk * s;
             }
             const bool valid = __shfl_sync(FULL, it, 0) < a.nitems;
             s = __shfl_sync(FULL, s, 0);
@@ -525,8 +536,11 @@ __global__ void __launch_bounds__(32 * (WY + 1), MINB) wave_kernel(const WaveArg
             const uint64_t t0 = lane == 0 ? global_ns() : 0;
 #pragma unroll 1
             while (true) {
+                if (!deps_ok) {
+                    deps_ok = deps.poll();
+                    if (deps_ok) __threadfence();  // acquire side of the counter polls
+                }
                 if (!prev_done) prev_done = mbar_test(&s_done, (uint32_t)((i - 1) & 1));
-                if (!deps_ok) deps_ok = deps.poll();
                 if (prev_done && deps_ok) break;
                 if (prev_done && !prev_released) {
                     release(prev_s, prev_b, prev_tile);
@@ -548,17 +562,16 @@ __global__ void __launch_bounds__(32 * (WY + 1), MINB) wave_kernel(const WaveArg
                 }
                 __nanosleep(32);
             }
-            if (!failed && valid) __threadfence();  // acquire side of the counter polls
-            const int go = (valid && !failed && ld_relaxed(a.abort) == 0) ? 1 : 0;
+            const int go = (valid && !failed) ? 1 : 0;
             if (lane == 0) {
                 s_job[i & 1][0] = s;
                 s_job[i & 1][1] = b;
                 s_job[i & 1][2] = tile;
                 s_job[i & 1][3] = go;
-                if (go) it = atomicAdd(a.ticket, 1);
             }
             __syncwarp();
             ready_arrive<kThreads>(i);
+            if (lane == 0 && go) it = atomicAdd(a.ticket, 1);
             if (!prev_released && !failed) release(prev_s, prev_b, prev_tile);
             if (!go) break;
             prev_s = s;

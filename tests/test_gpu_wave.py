@@ -52,7 +52,7 @@ def test_wave_bit_exact_every_depth(shape, dtype, wave_env):
     a = make_grid(nx, ny, nz, dtype)
     n = 13
     want = oracle_sweeps(a, n, nx, dtype)
-    for ring in (None, "1,3", "2,3", "3,4"):
+    for ring in (None, "1,3", "2,3", "3,4", "1,4", "2,5,3"):
         wave_env(ring)
         for t in (1, 2, 3, 4, 7, 13):
             got = run_wave(a, n, t, dtype, nx)
@@ -64,7 +64,7 @@ def test_wave_bit_exact_every_depth(shape, dtype, wave_env):
 def test_wave_inplace_bit_exact(shape, dtype, wave_env):
     nx, ny, nz = shape
     a = make_grid(nx, ny, nz, dtype)
-    for ring in (None, "1,3"):
+    for ring in (None, "1,3", "1,4", "2,5,3"):
         wave_env(ring)
         for n, t in ((2, 2), (3, 2), (5, 2), (13, 3), (13, 4), (9, 9)):
             want = oracle_sweeps(a, n, nx, dtype)
@@ -191,3 +191,20 @@ def test_full_size_512cubed_fp64_inplace():
     j.check()
     j.close()
     assert first_diff(out, want) is None, first_diff(out, want)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "bf16"])
+def test_wave_alternate_kernels_bit_exact(dtype, monkeypatch):
+    """The alternate instantiations of the pipelined kernel (other register caps
+    and load depths, chosen with JACOBI_WAVE_VARIANT) give the same bits."""
+    for shape in ((37, 29, 23), (130, 47, 9)):
+        nx, ny, nz = shape
+        a = make_grid(nx, ny, nz, dtype)
+        want = oracle_sweeps(a, 11, nx, dtype)
+        for v in ("0", "1"):
+            monkeypatch.setenv("JACOBI_WAVE_VARIANT", v)
+            for ring in ("1,3", "4,4"):
+                monkeypatch.setenv("JACOBI_WAVE", ring)
+                for t in (1, 3, 11):
+                    got = run_wave(a, 11, t, dtype, nx)
+                    assert first_diff(got, want) is None, (v, ring, t, first_diff(got, want))

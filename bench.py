@@ -71,7 +71,7 @@ def parse():
                    "(cases: sweep, rhs, residual, adjoint, batch: --size = number of grids, "
                    "peaks: the pipe-rate probes)")
     p.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
-    p.add_argument("--kernel", default="auto", choices=["auto", "plain", "tb"])
+    p.add_argument("--kernel", default="auto", choices=["auto", "plain", "tb", "wave"])
     p.add_argument("--size", type=int, default=NX)
     p.add_argument("--sweeps", type=int, default=NSWEEPS)
     p.add_argument("--slabs", action="store_true",
@@ -290,7 +290,8 @@ def variant_rows(dev, steps, model_in=None):
         tmax = _lib.jacobi_max_depth(code, _lib.JAC_OP_SWEEP)
         cases = [(1, api.JAC_KERNEL_PLAIN, "plain")] + \
             [(t, api.JAC_KERNEL_TB, f"tb_t{t}") for t in range(1, tmax + 1)] + \
-            [(16, api.JAC_KERNEL_TB, "tb_t16")]
+            [(16, api.JAC_KERNEL_TB, "tb_t16")] + \
+            [(t, api.JAC_KERNEL_WAVE, f"wave_t{t}") for t in (1, 2, 4, 8, 16)]
         plain_glups = None
         for t, kern, name in cases:
             try:
@@ -309,7 +310,10 @@ def variant_rows(dev, steps, model_in=None):
             else:
                 if dtype == "f64" and plain_glups:
                     row["multiple_of_plain"] = round(glups / plain_glups, 3)
-                if model_in is not None:
+                if kern == api.JAC_KERNEL_WAVE:
+                    row["planes_per_item"] = plan["kchunk"]
+                    row["ctas"] = plan["grid_x"]
+                elif model_in is not None:
                     es = {"f64": 8, "f32": 4, "bf16": 2}[dtype]
                     pred, bound = model.predict(
                         plan["t"], plan["ext_x"], plan["ext_y"], es, model_in["hbm_gbs"],
@@ -322,6 +326,18 @@ def variant_rows(dev, steps, model_in=None):
             rows[f"{dtype}_{name}"] = row
         j.close()
         del j
+        # the same workload on one grid, updated in place (half the memory)
+        ji = api.Jacobi(api.from_numpy(make_input(dtype), NX, dev), inplace=True)
+        ms = time_sweeps(ji, NSWEEPS, 4, api.JAC_KERNEL_WAVE, steps, 1, stream)
+        glups = NX * NY * NZ * NSWEEPS / ms / 1e6
+        row = {"glups": round(glups, 2), "ms_per_100_sweeps": round(ms, 3), "t_used": 4,
+               "grids": 1}
+        if dtype == "f64" and plain_glups:
+            row["multiple_of_plain"] = round(glups / plain_glups, 3)
+        rows[f"{dtype}_wave_inplace_t4"] = row
+        ji.check()
+        ji.close()
+        del ji
         torch.cuda.empty_cache()
     return rows
 
@@ -836,7 +852,7 @@ def run_case(args):
         return
     j = api.Jacobi(api.from_numpy(a, n, "cuda"))
     kern = {"auto": api.JAC_KERNEL_AUTO, "plain": api.JAC_KERNEL_PLAIN,
-            "tb": api.JAC_KERNEL_TB}[args.kernel]
+            "tb": api.JAC_KERNEL_TB, "wave": api.JAC_KERNEL_WAVE}[args.kernel]
     ms = time_sweeps(j, args.sweeps, args.t, kern, args.steps, args.warmup,
                      torch.cuda.current_stream())
     j.check()

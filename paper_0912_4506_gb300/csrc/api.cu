@@ -184,7 +184,25 @@ int run_wave(jacobi_s* h, int nsweeps, int t, int* final_is_b, jacobi_plan_info*
                 return JAC_ECUDA;
             a.wait_ns = 100000000ull;
         }
-        if (we->launch(a, w.ctas, h->stream) != cudaSuccess) return JAC_ECUDA;
+        // TMA-staged entries: boxes of the tile plus a 16-byte-aligned x halo and one
+        // row above and below, over the source grid and over the rings (levels
+        // 1..t-1 as one array of (t-1) rp planes in the grid's plane layout)
+        CUtensorMap map_src{}, map_ring{};
+        if (we->tma) {
+            const int box_x = 32 * we->V + 2 * (16 / elem_size(h->dtype));
+            const int box_y = we->WY + 2;
+            if (!encode_grid_map(&map_src, h->dtype, h->g, a.src, box_x, box_y))
+                return JAC_ECUDA;
+            map_ring = map_src;
+            if (w.t >= 2) {
+                Geom gr = h->g;
+                gr.nz = (w.t - 1) * w.rp - 2;
+                if (!encode_grid_map(&map_ring, h->dtype, gr, h->wbuf, box_x, box_y))
+                    return JAC_ECUDA;
+            }
+        }
+        if (we->launch(a, map_src, map_ring, w.ctas, h->stream) != cudaSuccess)
+            return JAC_ECUDA;
         if (!h->inplace) cur_b ^= 1;
     }
     if (final_is_b) *final_is_b = cur_b;

@@ -38,10 +38,6 @@ struct BatchArgs {
     unsigned long long wait_ns;
 };
 
-__device__ __forceinline__ void fence_proxy_async_global() {
-    asm volatile("fence.proxy.async.global;" ::: "memory");
-}
-
 template <class Tr, int V, int T>
 __device__ __forceinline__ void batch_tile(const CUtensorMap* map, const TBArgs& a, int bx,
                                            int by, int bz, unsigned char* smem, int* s_abort) {

@@ -177,6 +177,12 @@ __device__ __forceinline__ uint64_t global_ns() {
     return t;
 }
 
+// Orders this thread's view of global memory (data acquired from other CTAs'
+// ordinary stores) before its later TMA reads, which go through the async proxy.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
 // GPU-scope acquire load of a progress counter written by other CTAs.
 __device__ __forceinline__ int ld_acquire(const int* p) {
     int v;

@@ -44,14 +44,18 @@ struct PlainEntry {
 };
 
 struct WaveArgs;
-using WaveLaunchFn = cudaError_t (*)(const WaveArgs& a, int ctas, cudaStream_t st);
+// map_src: the source grid, map_ring: the rings (TMA-staged entries only)
+using WaveLaunchFn = cudaError_t (*)(const WaveArgs& a, const CUtensorMap& map_src,
+                                     const CUtensorMap& map_ring, int ctas, cudaStream_t st);
 
 // One instantiation of the pipelined (wavefront) kernel: tiles of 32*V x WY cells.
 struct WaveEntry {
     int dtype;
     int V;
     int WY;
-    int nemu;  // FP64: integer-pipe additions code (0: all on the FP64 unit)
+    int nemu;     // FP64: integer-pipe additions code (0: all on the FP64 unit)
+    int tma;      // 1: planes staged in shared memory by TMA (boxes of 32V + 2*16B x WY+2)
+    size_t smem;  // dynamic shared memory bytes
     WaveLaunchFn launch;
     const void* kernel;
 };

@@ -274,12 +274,12 @@ bool wave_plan(int dtype, const Geom& g, int t, const WaveEntry& e, int device, 
     WavePlan w{};
     if (t < 1 || t > kMaxWaveDepth) return false;
     w.t = t;
-    // FP64: interior-aligned cells 1..; FP32/bf16: vectors from x = 0 (cells 0..nx)
+    // FP64 (register march): interior-aligned cells 1..; FP32/bf16: cells from x = 0
     const int cells = dtype == JAC_F64 ? g.nx : g.nx + 1;
     w.ntx = (cells + 32 * e.V - 1) / (32 * e.V);
     w.nty = (g.ny + e.WY - 1) / e.WY;
     const size_t plane_bytes = (size_t)g.plane * (size_t)elem_size(dtype);
-    const size_t budget = (size_t)256 << 20;
+    const size_t budget = (size_t)512 << 20;
     w.R = 4;
     w.sk = 2;
     w.kb = 1;
@@ -306,7 +306,8 @@ bool wave_plan(int dtype, const Geom& g, int t, const WaveEntry& e, int device, 
     const long long nitems = (long long)t * w.nb * w.ntx * w.nty;
     if (nitems > (1LL << 30)) return false;
     w.nitems = (int)nitems;
-    const int occ = cached_occupancy(e.kernel, device, 32 * (e.WY + 1), 0, false);
+    const int occ = cached_occupancy(e.kernel, device, 32 * (e.WY + 1), e.smem,
+                                     e.smem > (size_t)48 * 1024);
     w.ctas = (int)std::min<long long>(nitems, (long long)num_sms * occ);
     w.ring_bytes = (size_t)(t - 1) * (size_t)w.rp * plane_bytes;
     w.sync_ints = (size_t)t * w.ntx * w.nty + 2;

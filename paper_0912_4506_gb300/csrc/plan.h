@@ -71,7 +71,8 @@ int plan_depths(int dtype, int mode, int nsweeps, int t, DepthPlan* out);
 
 // Pipelined (wavefront) passes.  A pass of depth t keeps levels 1..t-1 in ring
 // buffers of rp = R * kb planes each; kb (planes per work item) is the largest
-// power of two up to 32 whose rings fit the L2 budget (kb = 1 otherwise), R = 4,
+// power of two up to 32 whose rings fit 512 MB (kb = 1 otherwise; larger items
+// measured faster than rings held to the L2 size), R = 4,
 // ticket skew sk = 2.  JACOBI_WAVE="kb,R" or "kb,R,sk" overrides them
 // (measurement runs); sk defaults to min(2, R - 2) and must stay below R - 1.
 constexpr int kMaxWaveDepth = 32;

@@ -36,9 +36,11 @@
 //    place in the next level.  The boundary planes z = 0 and z = nz+1 of every
 //    level are read from the source grid, whose boundary layer no pass writes.
 //
-// Loads of the levels go through the coherent path (ld.global.ca): the data
-// was written during this launch by other CTAs, and the GPU-scope acquire of
-// the counters makes it visible to every thread of the CTA after the barrier.
+// The levels are read either by TMA into a shared-memory ring (FP32/bf16, the
+// default) or by the register march through the coherent path (ld.global.ca;
+// FP64): the data was written during this launch by other CTAs, and the GPU-scope
+// acquire of the counters makes it visible to every thread of the CTA after the
+// job barrier (and to the TMA unit after a proxy fence).
 // The arithmetic is Eq. 1 in its operand order, as in every other kernel, so
 // results are bit-identical to a sequential sweep loop.
 #pragma once
@@ -376,6 +378,183 @@ __device__ __forceinline__ bool wave_wait(const int* c, int target, const WaveAr
     return true;
 }
 
+// Named barriers: "job i published" from the control warp to the compute warps,
+// one per job parity so that consecutive jobs never share a barrier generation.
+// (Barrier numbers are immediates, so only barriers 0..3 are allocated; 3 is the
+// compute warps' step barrier of the TMA-staged march.)
+template <int ID, int N>
+__device__ __forceinline__ void named_sync() {
+    asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(N) : "memory");
+}
+template <int ID, int N>
+__device__ __forceinline__ void named_arrive() {
+    asm volatile("bar.arrive %0, %1;" ::"n"(ID), "n"(N) : "memory");
+}
+template <int N>
+__device__ __forceinline__ void ready_sync(int i) {
+    if (i & 1) named_sync<2, N>(); else named_sync<1, N>();
+}
+template <int N>
+__device__ __forceinline__ void ready_arrive(int i) {
+    if (i & 1) named_arrive<2, N>(); else named_arrive<1, N>();
+}
+
+// ---------------------------------------------------------------------------
+// TMA-staged march (FP32/bf16).  The register march above needs a register for
+// every load in flight, so its resident warps bound it.  Here the planes of an
+// item reach shared memory by TMA: one box per source plane, the tile's rows
+// y0-1 .. y0+WY and columns x0-XA .. x0+32V+XA-1 (XA cells = 16 bytes, so the box
+// starts aligned), into a ring of NS slots with one "full" mbarrier each.  Warp 0
+// issues the copies; after step m every compute warp passes a named barrier, and
+// warp 0 then refills the slot of source plane m with plane m+NS.  Phases run on
+// across items (a per-CTA count of the planes issued).
+constexpr int kWaveRing = 6;
+constexpr int kBarStep = 3;  // named barrier among the compute warps
+
+template <class S, int V, int WY>
+struct WaveTma {
+    static constexpr int XA = 16 / (int)sizeof(S);      // 16-byte alignment in cells
+    static constexpr int EXB = 32 * V + 2 * XA;         // box width (cells)
+    static constexpr int ROWS = WY + 2;                 // box height
+    static constexpr int BOX_BYTES = EXB * ROWS * (int)sizeof(S);
+    static constexpr int SLOT = (BOX_BYTES + 127) / 128 * 128;  // slot stride (bytes)
+    static constexpr int HEADER = 128;                  // NS mbarriers
+    static constexpr size_t bytes() { return HEADER + (size_t)kWaveRing * SLOT; }
+    static_assert(EXB * (int)sizeof(S) % 16 == 0, "box rows are whole 16-byte units");
+    static_assert(EXB <= 256 && ROWS <= 256, "TMA box dimensions");
+};
+
+// (FP64 keeps the register march: this march with the integer-pipe accumulator
+// measured 75 GLUP/s against 142 at 512^3.)
+template <class Tr, int V, int WY>
+__device__ __forceinline__ void wave_march_tma(const WaveArgs& a, const CUtensorMap* map_src,
+                                               const CUtensorMap* map_ring, int s, int k0,
+                                               int k1, int tx, int ty, unsigned char* smem,
+                                               uint32_t& issued) {
+    using S = typename Tr::S;
+    using C = typename Tr::C;
+    using VS = Vec<S, V>;
+    using Ly = WaveTma<S, V, WY>;
+    constexpr int NS = kWaveRing;
+    const Geom& g = a.g;
+    const int lane = threadIdx.x, warp = threadIdx.y;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+    unsigned char* ring = smem + Ly::HEADER;
+    const C c6 = Tr::sixth();
+    const long long px = g.px, plane = g.plane;
+
+    const int xt = 32 * V * tx;                 // first cell of the tile (x)
+    const int X0 = xt - Ly::XA, Y0 = ty * WY;   // box origin (x aligned, y = y0 - 1)
+    const int M = k1 - k0 + 3;                  // source planes k0-1 .. k1+1
+    const uint32_t first = issued;
+    const bool producer = warp == 0 && lane == 0;
+    auto issue = [&](int e) {  // source plane k0-1+e into the slot of entry first+e
+        const uint32_t ge = first + (uint32_t)e;
+        const int slot = (int)(ge % NS);
+        const int z = k0 - 1 + e;
+        mbar_arrive_expect_tx(&full[slot], Ly::BOX_BYTES);
+        void* dst = ring + slot * Ly::SLOT;
+        if (s == 1 || z == 0 || z == g.nz + 1)
+            tma_load_3d(dst, map_src, &full[slot], X0, Y0, z);
+        else
+            tma_load_3d(dst, map_ring, &full[slot], X0, Y0, (s - 2) * a.rp + (z - 1) % a.rp);
+    };
+    if (producer) {
+        // the item's inputs were acquired (control warp fence, then the job barrier)
+        // through the generic proxy; TMA reads them through the async proxy
+        fence_proxy_async_global();
+        for (int e = 0; e < NS && e < M; ++e) issue(e);
+    }
+    issued = first + (uint32_t)M;
+
+    const int y = 1 + ty * WY + warp;
+    const int x0 = xt + V * lane;
+    const bool row_ok = y <= g.ny;
+    const bool loadable = x0 + V <= g.px;
+    bool interior[V];
+    bool all_interior = true;
+#pragma unroll
+    for (int e = 0; e < V; ++e) {
+        interior[e] = loadable && x0 + e >= 1 && x0 + e <= g.nx;
+        all_interior = all_interior && interior[e];
+    }
+    const bool to_ring = s < a.t;
+    const bool row_lo = to_ring && row_ok && loadable && y == 1;
+    const bool row_hi = to_ring && row_ok && loadable && y == g.ny;
+    const bool edge_lo = to_ring && row_ok && lane == 0 && x0 == 1;
+    const bool edge_hi = to_ring && row_ok && lane == 31 && x0 + V == g.nx + 1 &&
+                         x0 + V < g.px;
+    S* dbase = to_ring ? static_cast<S*>(a.ring) + (long long)(s - 1) * a.rp * plane
+                       : static_cast<S*>(a.dst);
+    const long long row = g.lin(loadable ? x0 : 0, row_ok ? y : 1, 0);
+    const int col = Ly::XA + V * lane;  // the lane's first cell in a box row
+    auto at = [&](uint32_t ge, int r) -> const S* {
+        return reinterpret_cast<const S*>(ring + (int)(ge % NS) * Ly::SLOT) + r * Ly::EXB + col;
+    };
+    // bounded; returns at once when another wait of the launch has run out
+    auto wait = [&](uint32_t ge) {
+        uint64_t* bar = &full[ge % NS];
+        const uint32_t par = (ge / NS) & 1u;
+        if (mbar_try_wait(bar, par)) return;
+        const uint64_t t0 = global_ns();
+        while (!mbar_try_wait(bar, par)) {
+            if (ld_relaxed(a.abort) != 0) return;
+            if (global_ns() - t0 > a.wait_ns) {
+                wave_fail(a);
+                return;
+            }
+        }
+    };
+    wait(first);
+    wait(first + 1);
+#pragma unroll 1
+    for (int m = 0; m + 2 < M; ++m) {
+        const uint32_t e0 = first + (uint32_t)m;  // plane k-1; e0+1: plane k; e0+2: plane k+1
+        wait(e0 + 2);
+        const int k = k0 + m;
+        if (row_ok) {
+            const int r = warp + 1;
+            const VS dn = *reinterpret_cast<const VS*>(at(e0, r));
+            const VS ct = *reinterpret_cast<const VS*>(at(e0 + 1, r));
+            const VS up = *reinterpret_cast<const VS*>(at(e0 + 2, r));
+            const VS no = *reinterpret_cast<const VS*>(at(e0 + 1, r - 1));
+            const VS so = *reinterpret_cast<const VS*>(at(e0 + 1, r + 1));
+            const S el = at(e0 + 1, r)[-1];
+            const S er = at(e0 + 1, r)[V];
+            VS outv;
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                const C l = Tr::ld(e == 0 ? el : ct.v[e - 1]);
+                const C rr = Tr::ld(e == V - 1 ? er : ct.v[e + 1]);
+                C sum = Tr::add(l, rr);
+                sum = Tr::add(sum, Tr::ld(no.v[e]));
+                sum = Tr::add(sum, Tr::ld(so.v[e]));
+                sum = Tr::add(sum, Tr::ld(dn.v[e]));
+                sum = Tr::add(sum, Tr::ld(up.v[e]));
+                outv.v[e] = interior[e] ? Tr::st(Tr::mul(sum, c6)) : ct.v[e];
+            }
+            S* pd = dbase + (to_ring ? (long long)((k - 1) % a.rp) * plane
+                                     : (long long)k * plane) + row;
+            if (to_ring) {
+                if (loadable) *reinterpret_cast<VS*>(pd) = outv;
+                if (row_lo) *reinterpret_cast<VS*>(pd - px) = no;
+                if (row_hi) *reinterpret_cast<VS*>(pd + px) = so;
+                if (edge_lo) pd[-1] = el;
+                if (edge_hi) pd[V] = er;
+            } else if (all_interior) {
+                *reinterpret_cast<VS*>(pd) = outv;
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    if (interior[e]) pd[e] = outv.v[e];
+            }
+        }
+        // every compute warp is done with the slot of plane k-1: refill it
+        named_sync<kBarStep, 32 * WY>();
+        if (producer && m + NS < M) issue(m + NS);
+    }
+}
+
 // NEMU (FP64): 0 = every addition on the FP64 unit; kAccBaseWave + K + 8F = K
 // additions through the accumulator in word form F (when the range flag is set).
 constexpr int kAccBaseWave = 16;
@@ -431,26 +610,6 @@ __device__ __forceinline__ void wave_item(const WaveArgs& a, int s, int b, int t
     }
 }
 
-// Named barriers: "job i published" from the control warp to the compute warps,
-// one per job parity so that consecutive jobs never share a barrier generation.
-// (Barrier numbers are immediates, so only barriers 0..2 are allocated.)
-template <int ID, int N>
-__device__ __forceinline__ void named_sync() {
-    asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(N) : "memory");
-}
-template <int ID, int N>
-__device__ __forceinline__ void named_arrive() {
-    asm volatile("bar.arrive %0, %1;" ::"n"(ID), "n"(N) : "memory");
-}
-template <int N>
-__device__ __forceinline__ void ready_sync(int i) {
-    if (i & 1) named_sync<2, N>(); else named_sync<1, N>();
-}
-template <int N>
-__device__ __forceinline__ void ready_arrive(int i) {
-    if (i & 1) named_arrive<2, N>(); else named_arrive<1, N>();
-}
-
 // "job i computed": an mbarrier with one arrival per compute warp; phase i
 // completes when job i is done.  Non-blocking test, so that the control warp
 // can watch it while it polls the counters of the next job.
@@ -478,16 +637,27 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // So the checks of job i overlap the arithmetic of job i-1.  A CTA holds at most
 // two unreleased tickets and every wait is on a smaller ticket: the pass makes
 // progress for any number of CTAs.
-template <class Tr, int V, int WY, int NEMU, int MINB>
-__global__ void __launch_bounds__(32 * (WY + 1), MINB) wave_kernel(const WaveArgs a) {
+// TMA = 1: the compute warps use the TMA-staged march (FP32/bf16) with the maps
+// of the source grid and of the rings; TMA = 0: the register march (maps unused).
+template <class Tr, int V, int WY, int NEMU, int MINB, int TMA>
+__global__ void __launch_bounds__(32 * (WY + 1), MINB)
+    wave_kernel(const WaveArgs a, const __grid_constant__ CUtensorMap map_src,
+                const __grid_constant__ CUtensorMap map_ring) {
     const unsigned FULL = 0xffffffffu;
     constexpr int kThreads = 32 * (WY + 1);
+    extern __shared__ __align__(1024) unsigned char wsmem[];
     __shared__ int s_job[2][4];  // s, b, tile, go
     __shared__ __align__(8) uint64_t s_done;
     const int lane = threadIdx.x;
     const int ntiles = a.ntx * a.nty;
     if (threadIdx.y == WY && lane == 0) {
         mbar_init(&s_done, WY);
+        if constexpr (TMA) {
+            uint64_t* full = reinterpret_cast<uint64_t*>(wsmem);
+            for (int i = 0; i < kWaveRing; ++i) mbar_init(&full[i], 1);
+            prefetch_tmap(&map_src);
+            prefetch_tmap(&map_ring);
+        }
         fence_mbar_init();
     }
     __syncthreads();
@@ -583,12 +753,21 @@ __global__ void __launch_bounds__(32 * (WY + 1), MINB) wave_kernel(const WaveArg
 
     // ---- compute warps
     const bool fast = a.fast != nullptr && *a.fast != 0;
+    uint32_t issued = 0;  // TMA march: source planes issued so far (mbarrier phases)
 #pragma unroll 1
     for (int i = 0;; ++i) {
         ready_sync<kThreads>(i);
         if (!s_job[i & 1][3]) break;
         const int s = s_job[i & 1][0], b = s_job[i & 1][1], tile = s_job[i & 1][2];
-        wave_item<Tr, V, WY, NEMU>(a, s, b, tile, fast);
+        if constexpr (TMA) {
+            const int k0 = 1 + b * a.kb;
+            const int k1 = min(a.g.nz, k0 + a.kb - 1);
+            static_assert(sizeof(typename Tr::S) < 8, "FP64 uses the register march");
+            wave_march_tma<Tr, V, WY>(a, &map_src, &map_ring, s, k0, k1, tile % a.ntx,
+                                      tile / a.ntx, wsmem, issued);
+        } else {
+            wave_item<Tr, V, WY, NEMU>(a, s, b, tile, fast);
+        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&s_done);
     }

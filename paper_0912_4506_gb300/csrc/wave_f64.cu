@@ -8,8 +8,8 @@
 namespace jac {
 
 static const WaveEntry kWave[] = {
-    JAC_WAVE(F64, 2, 8, kAccBaseWave + 4 + 8 * 3, 4),
-    JAC_WAVE(F64, 2, 8, kAccBaseWave + 4 + 8 * 3, 3),
+    JAC_WAVE(F64, 2, 8, kAccBaseWave + 4 + 8 * 3, 4, 0),
+    JAC_WAVE(F64, 2, 8, kAccBaseWave + 4 + 8 * 3, 3, 0),
 };
 const WaveEntry* wave_entries_f64(int* n) {
     *n = (int)(sizeof(kWave) / sizeof(kWave[0]));

@@ -201,7 +201,7 @@ def test_wave_alternate_kernels_bit_exact(dtype, monkeypatch):
         nx, ny, nz = shape
         a = make_grid(nx, ny, nz, dtype)
         want = oracle_sweeps(a, 11, nx, dtype)
-        for v in ("0", "1"):
+        for v in ("0", "1", "2"):
             monkeypatch.setenv("JACOBI_WAVE_VARIANT", v)
             for ring in ("1,3", "4,4"):
                 monkeypatch.setenv("JACOBI_WAVE", ring)

@@ -289,8 +289,9 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
                           MODE == MODE_PLAIN;
     // FP32 arithmetic (FP32 and bf16 storage) on pairs of cells
     // (FP32 storage, depths 1-2, CTAs of at most 16 warps: measured 707 / 950 against
-    // 693 / 924 GLUP/s at 512^3; deeper or 1024-thread kernels spill with it, and
-    // bf16 storage ran slower)
+    // 693 / 924 GLUP/s at 512^3; 1024-thread kernels spill with it, bf16 storage ran
+    // slower, and depth 3 on 24 / 20 / 16-warp tiles, which fit it without spills,
+    // ran at 926 / 850 / 707 against 993 for the unpacked 32-warp tile)
     constexpr bool kPacked = kPackedF32 && std::is_same<S, float>::value && V % 2 == 0 &&
                              T <= 2 && NW <= 16;
     // addition number idx (0..4) of an update: the first EMU on the integer pipes

@@ -17,9 +17,9 @@ JAC_TABLE(tb_entries_f64, kTB)
 // 5 additions one at a time on the integer pipes (emu.cuh); 16 + K + 8F sends the
 // first K additions through the unpacked accumulator (emusum.cuh) in word form F,
 // and + 32 compiles it for 5 resident CTAs per SM (at most 51 registers).  76
-// (K = 4, F = 3, capped) measured fastest at 512^3 on GB300: 201 GLUP/s, against
-// 193 for F = 0 capped, 197 for F = 0, 167 / 156 with K = 3 / 5, 166 for entry 6
-// and 85 for entry 0.
+// (K = 4, F = 3, capped) measured fastest at 512^3 on GB300: 202 GLUP/s, against
+// 200 for F = 2 capped, 195 for F = 1 capped, 194 for F = 0 capped, 197 for F = 0,
+// 167 / 156 with K = 3 / 5, 166 for entry 6 and 85 for entry 0.
 static const PlainEntry kPlain[] = {JAC_PLAIN(F64, 2, 8, 0),  JAC_PLAIN(F64, 2, 8, 6),
                                     JAC_PLAIN(F64, 2, 8, 19), JAC_PLAIN(F64, 2, 8, 20),
                                     JAC_PLAIN(F64, 2, 8, 21), JAC_PLAIN(F64, 2, 8, 44),

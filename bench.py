@@ -11,12 +11,13 @@ the previous step's result; the work per step is identical.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 (torchrun, one rank per GPU): every rank runs its own grid (replicas,
-weak scaling, no collective on the data path); value = all ranks' lattice-site
-updates / max-over-ranks time.  With --slabs the ranks instead share one grid of
-512 x 512 x 512N cells cut into z-slabs (Sect. 2.1), halos exchanged by NCCL.  --impl reference times the CPU oracle (the
-reference statement of the method) on the host cores on a bounded sample of the
-same workload.
+N > 1 (torchrun, one rank per GPU): the ranks share one grid of 512 x 512 x 512N
+cells cut into z-slabs of 512 planes (Sect. 2.1, weak scaling): every 4 sweeps
+each rank exchanges 5 halo planes with its neighbours by NCCL send/recv, then
+sweeps its slab; value = all ranks' core lattice-site updates / max-over-ranks
+time.  --replicas runs independent grids instead.  --impl reference times the
+CPU oracle (the reference statement of the method) on the host cores on a
+bounded sample of the same workload.
 """
 import argparse
 import json
@@ -31,6 +32,7 @@ sys.path.insert(0, ROOT)
 
 NX = NY = NZ = 512
 NSWEEPS = 100
+SLAB_H = 4  # halo planes of the z-slab decomposition (N > 1)
 ALGO_BYTES_PER_LUP = {"f64": 16, "f32": 8, "bf16": 4}
 
 # DRAM bytes per launch of the dominant kernel, from an ncu capture of the same
@@ -74,9 +76,9 @@ def parse():
     p.add_argument("--kernel", default="auto", choices=["auto", "plain", "tb", "wave"])
     p.add_argument("--size", type=int, default=NX)
     p.add_argument("--sweeps", type=int, default=NSWEEPS)
-    p.add_argument("--slabs", action="store_true",
-                   help="with N ranks: one z-slab of a 512 x 512 x (512 N) FP64 grid per rank, "
-                        "halos exchanged by NCCL send/recv (weak scaling), instead of replicas")
+    p.add_argument("--replicas", action="store_true",
+                   help="N > 1: independent 512^3 grids per rank (no halo exchange) instead "
+                        "of the z-slab decomposition of one 512 x 512 x 512N grid")
     return p.parse_args()
 
 
@@ -555,13 +557,40 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
     plan = j.plan(NSWEEPS, args.t, api.JAC_KERNEL_AUTO)
     launches_per_step = plan["passes"]
+    range_checks_per_step = 1 if plan.get("emu_adds", 0) > 0 else 0
+
+    # N > 1: one grid of 512 x 512 x 512N cells cut into z-slabs, one per rank
+    # (Sect. 2.1): every SLAB_H sweeps the ranks exchange SLAB_H + 1 halo planes
+    # with their neighbours by NCCL send/recv, then sweep their slab (core plus
+    # halos) with the library's FP64 choice.  --replicas: independent grids.
+    rs = None
+    if world > 1 and not args.replicas:
+        from paper_0912_4506_gb300 import inputs, slabs
+        nzg = NZ * world
+        z0, z1 = slabs.slab_ranges(nzg, world)[rank]
+        lo, hi = slabs.slab_extent(z0, z1, nzg, SLAB_H)
+        a_slab = inputs.uniform_grid_f64(NX, NY, nzg, px=inputs.row_pitch(NX, "f64"),
+                                         planes=(lo, hi))
+        rs = slabs.RankSlab(NX, NY, nzg, SLAB_H, torch.from_numpy(a_slab).to(dev), rank,
+                            world)
+        kt = args.t if args.t > 0 else 1
+        npasses = len(rs.passes(NSWEEPS, SLAB_H))
+        launches_per_step = NSWEEPS if kt == 1 else sum(
+            -(-d // min(kt, d)) for d in rs.passes(NSWEEPS, SLAB_H))
+        range_checks_per_step *= npasses
+
+    def step():
+        if rs is not None:
+            rs.sweep(NSWEEPS, SLAB_H, kt)
+        else:
+            j.sweep(NSWEEPS, args.t)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
     for _ in range(args.warmup):
-        j.sweep(NSWEEPS, args.t)
+        step()
     torch.cuda.synchronize()
     barrier()
     gpu_uuid = torch.cuda.get_device_properties(dev).uuid
@@ -574,7 +603,7 @@ def run_ours(args):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for _ in range(args.steps):
-        j.sweep(NSWEEPS, args.t)
+        step()
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
@@ -588,27 +617,53 @@ def run_ours(args):
     # runs 100 sweeps and downloads its result; steps alternate between two
     # handles on two streams (api.HostPipeline), so a step's copies overlap the
     # neighbouring step's sweeps.  Two pinned input and output buffers alternate.
-    host_in = [torch.from_numpy(a64).pin_memory() for _ in range(2)]
-    host_out = [torch.empty_like(host_in[0]).pin_memory() for _ in range(2)]
-    pipe = api.HostPipeline(NX, NY, NZ, "f64", dev)
-    pipe.run(host_in, host_out, NSWEEPS, args.t)
-    torch.cuda.synchronize()
-    barrier()
-    e2 = torch.cuda.Event(enable_timing=True)
-    e3 = torch.cuda.Event(enable_timing=True)
-    e2.record(stream)
-    pipe.run([host_in[i % 2] for i in range(args.steps)],
-             [host_out[i % 2] for i in range(args.steps)], NSWEEPS, args.t)
-    e3.record(stream)
-    torch.cuda.synchronize()
-    barrier()
+    if rs is None:
+        host_in = [torch.from_numpy(a64).pin_memory() for _ in range(2)]
+        host_out = [torch.empty_like(host_in[0]).pin_memory() for _ in range(2)]
+        pipe = api.HostPipeline(NX, NY, NZ, "f64", dev)
+        pipe.run(host_in, host_out, NSWEEPS, args.t)
+        torch.cuda.synchronize()
+        barrier()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        e2.record(stream)
+        pipe.run([host_in[i % 2] for i in range(args.steps)],
+                 [host_out[i % 2] for i in range(args.steps)], NSWEEPS, args.t)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        nbytes_in = nbytes_out = host_in[0].numel() * host_in[0].element_size()
+        overlap = "2 handles on 2 streams: a step's copies overlap the next step's sweeps"
+        pipe.close()
+    else:
+        # every step: this rank's slab from pinned host memory, the decomposed
+        # sweeps, this rank's core planes back to the host
+        host_in = torch.from_numpy(a_slab).pin_memory()
+        host_out = torch.empty_like(rs.core()).pin_memory()
+        e2 = torch.cuda.Event(enable_timing=True)
+        e3 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        barrier()
+        e2.record(stream)
+        for _ in range(args.steps):
+            rs.current().copy_(host_in, non_blocking=True)
+            step()
+            host_out.copy_(rs.core(), non_blocking=True)
+        e3.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        nbytes_in = host_in.numel() * host_in.element_size()
+        nbytes_out = host_out.numel() * host_out.element_size()
+        overlap = "none: upload, sweeps with halo exchanges, download in order"
     ms_e2e, _ = replica_throughput(e2.elapsed_time(e3), lups * args.steps, dev)
     e2e_value = lups * world / (ms_e2e / args.steps / 1e3) / 1e9
-    nbytes = host_in[0].numel() * host_in[0].element_size()
-    pipe.close()
 
+    if rs is not None:
+        rs.close()
     if rank != 0:
         j.close()
+        if world > 1:
+            torch.distributed.destroy_process_group()
         return
 
     pk, pk_src = peaks()
@@ -647,19 +702,21 @@ def run_ours(args):
         "value": round(value, 3), "unit": "GLUP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(ms_step, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "nx": NX, "ny": NY, "nz": NZ,
+        "config": {"workload": WORKLOAD if rs is None
+                   else f"jacobi7pt_512x512x{NZ * world}_fp64_100sweeps_zslabs",
+                   "nx": NX, "ny": NY, "nz": NZ if rs is None else NZ * world,
                    "sweeps_per_step": NSWEEPS, "plan": plan,
-                   "parallelism": "replicas" if world > 1 else "single",
+                   "parallelism": ("single" if world == 1 else "replicas" if rs is None
+                                   else f"z-slabs x {world}, {SLAB_H}-plane halos by NCCL "
+                                        f"send/recv every {SLAB_H} sweeps"),
                    "l2": "inputs larger than L2 (1.09 GB per grid), no flush"},
         "roofline": roof,
         # the sweep passes plus, for the FP64 sweep with integer-pipe additions,
         # the range check launched once per sweep call
-        "gpu_launches": (launches_per_step + (1 if plan.get("emu_adds", 0) > 0 else 0))
-                        * args.steps,
+        "gpu_launches": (launches_per_step + range_checks_per_step) * args.steps,
         "e2e": {"value": round(e2e_value, 3), "unit": "GLUP/s",
-                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-                "overlap": "2 handles on 2 streams: a step's copies overlap the next "
-                           "step's sweeps"},
+                "h2d_bytes_per_step": nbytes_in, "d2h_bytes_per_step": nbytes_out,
+                "overlap": overlap},
         "clocks": clocks,
         "peaks": pk_src,
     }
@@ -680,65 +737,8 @@ def run_ours(args):
         line["cpu_baseline"] = {"value": round(rate, 4), "unit": "GLUP/s", "cores": cores,
                                 "kind": "oracle", "sample": sample}
     print(json.dumps(line), flush=True)
-
-
-def run_slabs(args):
-    """The z-slab decomposition across ranks (Sect. 2.1): a 512 x 512 x (512 N) FP64
-    grid, one slab of 512 core planes per rank, h = 4 halo planes exchanged with
-    the neighbouring ranks by NCCL send/recv every 4 sweeps (5 planes per side),
-    the sweeps in between the library's FP64 choice (plain sweeps, depth --t),
-    100 sweeps per step.  value = all ranks' lattice-site updates / max-over-ranks
-    time (weak scaling)."""
-    import torch
-    import torch.distributed as dist
-    from paper_0912_4506_gb300 import inputs, slabs
-    world, rank, local = dist_setup()
     if world > 1:
-        dist.init_process_group("nccl", init_method="env://")
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    h = 4
-    kt = args.t if args.t > 0 else 1
-    nzg = NZ * world
-    z0, z1 = slabs.slab_ranges(nzg, world)[rank]
-    lo, hi = slabs.slab_extent(z0, z1, nzg, h)
-    a = inputs.uniform_grid_f64(NX, NY, nzg, px=inputs.row_pitch(NX, "f64"), planes=(lo, hi))
-    rs = slabs.RankSlab(NX, NY, nzg, h, torch.from_numpy(a).to(dev), rank, world)
-    del a
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-
-    for _ in range(args.warmup):
-        rs.sweep(NSWEEPS, h, kt)
-    torch.cuda.synchronize()
-    barrier()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(args.steps):
-        rs.sweep(NSWEEPS, h, kt)
-    e1.record()
-    torch.cuda.synchronize()
-    barrier()
-    lups = NX * NY * NZ * NSWEEPS  # per rank
-    ms, _ = replica_throughput(e0.elapsed_time(e1), lups * args.steps, dev)
-    value = lups * world * args.steps / (ms / 1e3) / 1e9
-    rs.close()
-    if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": round(value, 3), "unit": "GLUP/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"jacobi7pt_512x512x{nzg}_fp64_100sweeps_zslabs",
-                       "nx": NX, "ny": NY, "nz": nzg, "sweeps_per_step": NSWEEPS,
-                       "parallelism": f"z-slabs x {world}", "halo_planes": h,
-                       "sweep_depth": kt,
-                       "l2": "inputs larger than L2"}}), flush=True)
-    if world > 1:
-        dist.destroy_process_group()
+        torch.distributed.destroy_process_group()
 
 
 def run_case(args):
@@ -869,7 +869,5 @@ if __name__ == "__main__":
         run_case(a)
     elif a.impl == "reference":
         run_reference(a)
-    elif a.slabs:
-        run_slabs(a)
     else:
         run_ours(a)

@@ -36,6 +36,8 @@ struct jacobi_s {
     int rho_box_x, rho_box_y;
     void* fbuf;           // adjoint: face values per sweep (owned, grown on demand)
     size_t fbuf_bytes;
+    cudaStream_t side;    // adjoint: face bands run beside the passes (created on first use)
+    cudaEvent_t ev_in, ev_band;
     int inplace;          // one grid (jacobi_create_inplace): b == nullptr
     void* wbuf;           // pipelined passes: rings and counters (owned, grown on demand)
     size_t wbuf_bytes;
@@ -274,8 +276,12 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         return JAC_OK;
     }
 
+    // The adjoint sweep (transposed Eq. 1 on lambda with a zero boundary) is the
+    // plain sweep on the handle's grids: it runs on the plain blocked kernels, and
+    // its boundary-gradient face values come from launch_face_band per pass.
+    const int kmode = mode == MODE_ADJ ? MODE_PLAIN : mode;
     DepthPlan dp;
-    const int rc = plan_depths(h->dtype, mode, nsweeps, t, &dp);
+    const int rc = plan_depths(h->dtype, kmode, nsweeps, t, &dp);
     if (rc != JAC_OK) return rc;
     const long long slots_per_sm = h->num_sms;
 
@@ -285,7 +291,7 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         info_only->passes = dp.passes();
         if (dp.passes() > 0) {
             const int t0 = dp.depth(0);
-            const TBEntry* e = tb_entry(h->dtype, mode, t0);
+            const TBEntry* e = tb_entry(h->dtype, kmode, t0);
             const TileGeom gm = tile_geom(h->dtype, h->g, e->V, e->NW, e->T,
                                           slots_per_sm * tb_occupancy(*e, h->device), 0);
             info_only->t = t0;
@@ -331,13 +337,29 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         const size_t need = (size_t)fstride * (size_t)nsweeps * (size_t)elem_size(h->dtype);
         const int grc = grow_buffer(h, &h->fbuf, &h->fbuf_bytes, need);
         if (grc != JAC_OK) return grc;
+        if (!h->side) {
+            if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_band, cudaEventDisableTiming) != cudaSuccess)
+                return JAC_ECUDA;
+        }
     }
 
     int cur_b = 0;  // 0: current data in A
     int sweep0 = 0;
     for (int p = 0; p < dp.passes(); ++p) {
-        const TBEntry* e = tb_entry(h->dtype, mode, dp.depth(p));
+        const TBEntry* e = tb_entry(h->dtype, kmode, dp.depth(p));
         if (!e) return JAC_EUNSUPPORTED;
+        // adjoint: the face values of this pass's levels come from its input; the band
+        // kernel runs on the side stream beside the pass (both only read the input),
+        // and the next pass, which overwrites that input, waits for it
+        if (mode == MODE_ADJ &&
+            (cudaEventRecord(h->ev_in, h->stream) != cudaSuccess ||
+             cudaStreamWaitEvent(h->side, h->ev_in, 0) != cudaSuccess ||
+             launch_face_band(h->dtype, cur_b ? h->b : h->a, h->g, h->fbuf, fstride, sweep0,
+                              e->T, h->side) != cudaSuccess ||
+             cudaEventRecord(h->ev_band, h->side) != cudaSuccess))
+            return JAC_ECUDA;
         const TileGeom gm = tile_geom(h->dtype, h->g, e->V, e->NW, e->T,
                                       slots_per_sm * tb_occupancy(*e, h->device), 0);
         if (!gm.ok) return JAC_EUNSUPPORTED;
@@ -353,9 +375,6 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         args.g = h->g;
         args.dst = cur_b ? h->a : h->b;
         args.grad = grad;
-        args.fbuf = h->fbuf;
-        args.fstride = fstride;
-        args.sweep0 = sweep0;
         args.ox = gm.ox;
         args.x0_first = gm.x0_first;
         args.kz = gm.kz;
@@ -373,6 +392,8 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         const CUtensorMap& map_rho = mode == MODE_RHS ? h->map_rho : map;
         if (e->launch(map, map_rho, args, dim3(gm.ntx, gm.nty, gm.nchunk), h->stream) !=
             cudaSuccess)
+            return JAC_ECUDA;
+        if (mode == MODE_ADJ && cudaStreamWaitEvent(h->stream, h->ev_band, 0) != cudaSuccess)
             return JAC_ECUDA;
         cur_b ^= 1;
         sweep0 += e->T;
@@ -547,6 +568,12 @@ int jacobi_destroy(jacobi_t h) {
     cudaFree(h->status);
     if (h->fbuf) cudaFree(h->fbuf);
     if (h->wbuf) cudaFree(h->wbuf);
+    if (h->side) {
+        cudaStreamSynchronize(h->side);
+        cudaEventDestroy(h->ev_in);
+        cudaEventDestroy(h->ev_band);
+        cudaStreamDestroy(h->side);
+    }
     delete h;
     return JAC_OK;
 }
@@ -568,7 +595,9 @@ const char* jacobi_strerror(int code) {
 int jacobi_max_depth(int dtype, int op) {
     if (dtype < JAC_F64 || dtype > JAC_BF16 || op < JAC_OP_SWEEP || op > JAC_OP_ADJOINT)
         return JAC_EINVAL;
-    const int mode = op == JAC_OP_SWEEP ? MODE_PLAIN : op == JAC_OP_RHS ? MODE_RHS : MODE_ADJ;
+    // the adjoint runs on the plain sweep's kernels (run_passes); bf16 has none
+    if (op == JAC_OP_ADJOINT && dtype == JAC_BF16) return 0;
+    const int mode = op == JAC_OP_RHS ? MODE_RHS : MODE_PLAIN;
     return max_depth(dtype, mode);
 }
 

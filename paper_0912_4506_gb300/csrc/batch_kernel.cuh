@@ -85,9 +85,6 @@ __global__ void __launch_bounds__(kBatchNW * 32, 1) tb_batch_kernel(const BatchA
         a.g = G.g;
         a.dst = (item.pass & 1) ? G.a : G.b;
         a.grad = nullptr;
-        a.fbuf = nullptr;
-        a.fstride = 0;
-        a.sweep0 = 0;
         a.ox = pg.ox;
         a.x0_first = pg.x0_first;
         a.kz = pg.kz;

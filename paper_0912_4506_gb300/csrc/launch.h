@@ -63,10 +63,8 @@ struct WaveEntry {
 // Tables provided by the per-dtype translation units.
 const TBEntry* tb_entries_f64(int* n);
 const TBEntry* tb_entries_f64_deep(int* n);
-const TBEntry* tb_entries_f64_adj(int* n);
 const TBEntry* tb_entries_f32(int* n);
 const TBEntry* tb_entries_f32_rhs(int* n);
-const TBEntry* tb_entries_f32_adj(int* n);
 const TBEntry* tb_entries_bf16(int* n);
 const TBEntry* tb_entries_bf16_rhs(int* n);
 const PlainEntry* plain_entry_f64();
@@ -82,6 +80,8 @@ cudaError_t launch_boundary_copy(int dtype, const void* A, void* B, const Geom& 
                                  cudaStream_t st);
 cudaError_t launch_face_reduce(int dtype, void* grad, const Geom& g, const void* fbuf,
                                long long fstride, int nsweeps, cudaStream_t st);
+cudaError_t launch_face_band(int dtype, const void* src, const Geom& g, void* fbuf,
+                             long long fstride, int sweep0, int T, cudaStream_t st);
 cudaError_t launch_range_check(const double* A, const Geom& g, int* flag, cudaStream_t st);
 cudaError_t launch_residual(const double* u_in, double* u_out, const Geom& gu,
                             const void* e, void* rho, int lo_dtype, const Geom& glo,

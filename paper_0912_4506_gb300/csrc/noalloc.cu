@@ -134,9 +134,6 @@ extern "C" int jacobi_sweep_noalloc(int nx, int ny, int nz, int dtype, void* gri
             a.g = g;
             a.dst = cur_other ? grid : other;
             a.grad = nullptr;
-            a.fbuf = nullptr;
-            a.fstride = 0;
-            a.sweep0 = 0;
             a.ox = gm.ox;
             a.x0_first = gm.x0_first;
             a.kz = gm.kz;

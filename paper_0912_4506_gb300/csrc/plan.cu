@@ -67,10 +67,8 @@ const Tables& tables() {
         const TBEntry* p;
         p = tb_entries_f64(&n); add(p, n);
         p = tb_entries_f64_deep(&n); add(p, n);
-        p = tb_entries_f64_adj(&n); add(p, n);
         p = tb_entries_f32(&n); add(p, n);
         p = tb_entries_f32_rhs(&n); add(p, n);
-        p = tb_entries_f32_adj(&n); add(p, n);
         p = tb_entries_bf16(&n); add(p, n);
         p = tb_entries_bf16_rhs(&n); add(p, n);
         // the deepest depth reachable without a gap (a table with a gap would

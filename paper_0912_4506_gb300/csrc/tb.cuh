@@ -34,10 +34,10 @@
 // per-cell boundary selects.
 //
 // Modes: MODE_PLAIN (Eq. 1), MODE_RHS (the refinement's correction sweep, adds
-// rho before the product; rho's planes arrive by TMA beside the grid's), MODE_ADJ
-// (the adjoint sweep on a zero boundary; RN(1/6)*lambda at the face-neighbouring
-// interior cells of every level goes to a face buffer, read from shared memory
-// after each step's barrier, outside the k-march).
+// rho before the product; rho's planes arrive by TMA beside the grid's).  MODE_ADJ
+// names the adjoint operation for the planner: the adjoint sweep is the plain
+// sweep on lambda with a zero boundary, so it runs on the MODE_PLAIN kernels, and
+// its boundary-gradient face values come from a separate band kernel (aux.cu).
 #pragma once
 
 #include <type_traits>
@@ -61,9 +61,6 @@ struct TBArgs {
     Geom g;
     void* dst;          // output grid of the pass (level T)
     void* grad;         // gradient grid (only the never-executed hook below names it)
-    void* fbuf;         // MODE_ADJ: face buffer, c * lambda at face-adjacent cells
-    long long fstride;  // MODE_ADJ: elements per sweep in fbuf (all six faces)
-    int sweep0;         // MODE_ADJ: sweep index of this pass's level 0 in fbuf
     int ox;             // output tile width (multiple of the TMA alignment)
     int x0_first;       // x origin of tile 0's extended tile (aligned, may be < 0)
     int kz;             // output k-planes per CTA
@@ -189,69 +186,6 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
     S* dst = static_cast<S*>(a.dst);
     const long long rowoff = (long long)gy * g.px + gx0;  // valid only when used
     const int mycol = w * EX + lane * V;
-    // boundary gradient (MODE_ADJ): the output tile's cells in x and y, and which
-    // faces of the interior it touches (x = 1, x = nx, y = 1, y = ny)
-    const int cx0 = max(ox0, 1), cx1 = min(ox0 + a.ox, g.nx + 1);
-    const int cy0 = max(oy0, 1), cy1 = min(oy0 + OY, g.ny + 1);
-    const int ncols = max(cx1 - cx0, 0), nrows = max(cy1 - cy0, 0);
-    const int nfx = (MODE == MODE_ADJ) ? (int)(cx0 == 1) + (int)(cx1 == g.nx + 1) : 0;
-    const int nfy = (MODE == MODE_ADJ) ? (int)(cy0 == 1) + (int)(cy1 == g.ny + 1) : 0;
-    const int nxy = nfx * nrows + nfy * ncols;  // face cells per plane and level
-    static_assert(MODE != MODE_ADJ || 2 * EX + 2 * EY <= NW * 32,
-                  "one x/y face cell per thread at most");
-    // Thread tid < nxy owns one x/y face cell of the output tile for the whole tile:
-    // its offset in a shared-memory plane, and its place in a face-buffer row
-    // (base at plane 1, stride per plane).
-    const long long fxs = (long long)g.ny * g.nz, fys = (long long)g.nx * g.nz;
-    int f_sm = -1, f_qs = 0, f_base = 0;  // a face row has < 2^31 cells
-    if (MODE == MODE_ADJ && tid < nxy) {
-        int x, y, f, r = tid;
-        if (r < nfx * nrows) {
-            const int lo = (cx0 == 1) ? 1 : 0;  // which x faces the tile has
-            f = (lo && r >= nrows) ? 1 : (lo ? 0 : 1);
-            x = f == 0 ? 1 : g.nx;
-            y = cy0 + (r >= nrows ? r - nrows : r);
-            f_base = (int)(f * fxs) + (y - 1) - g.ny;  // plane q adds q * ny
-            f_qs = g.ny;
-        } else {
-            r -= nfx * nrows;
-            const int lo = (cy0 == 1) ? 1 : 0;
-            f = 2 + ((lo && r >= ncols) ? 1 : (lo ? 0 : 1));
-            y = f == 2 ? 1 : g.ny;
-            x = cx0 + (r >= ncols ? r - ncols : r);
-            f_base = (int)(2 * fxs + (f - 2) * fys) + (x - 1) - g.nx;  // plane q adds q * nx
-            f_qs = g.nx;
-        }
-        f_sm = (y - Y0) * EX + (x - X0);
-    }
-    // After the barrier of a step, the planes every level produced in it are in
-    // shared memory: level 0 in the ring slot, level s in its level buffer.  For
-    // each level s < T whose plane q is one of this CTA's planes, the face-adjacent
-    // cells of the output tile give c * lambda to the face buffer (one store per
-    // cell and sweep, no atomics); a separate kernel adds them to the gradient in
-    // sweep order.
-    auto adj_faces = [&](const S* plane_s, int s, int q) {
-        if constexpr (MODE == MODE_ADJ) {
-            if (q < kz0 || q >= kz1) return;
-            S* fb = static_cast<S*>(a.fbuf) + (long long)(a.sweep0 + s) * a.fstride;
-            if (f_sm >= 0)
-                fb[f_base + q * f_qs] = Tr::st(Tr::mul(c6, Tr::ld(plane_s[f_sm])));
-            // z faces: plane 1 feeds face z = 0, plane nz face z = nz+1 (both if nz = 1);
-            // every thread stores its own output cells of the plane
-            if (q == 1 || q == g.nz) {
-#pragma unroll
-                for (int zf = 0; zf < 2; ++zf) {
-                    if (q != (zf == 0 ? 1 : g.nz)) continue;
-                    S* face = fb + 2 * fxs + 2 * fys + zf * (long long)g.nx * g.ny +
-                              (long long)(gy - 1) * g.nx + (gx0 - 1);
-#pragma unroll
-                    for (int e = 0; e < V; ++e)
-                        if (outxy[e]) face[e] = Tr::st(Tr::mul(c6, Tr::ld(plane_s[mycol + e])));
-                }
-            }
-        }
-    };
-
     // Never executed: a per-level reduction hook (global reductions into the
     // gradient grid, unreachable in every mode), called at every level of the
     // k-march.  Kept because its presence changes how nvcc 13.0 schedules the
@@ -466,17 +400,6 @@ __device__ __forceinline__ bool tb_tile(const CUtensorMap* tmap, const CUtensorM
         }
         __syncthreads();
         if (*s_abort) return false;
-        if constexpr (MODE == MODE_ADJ) {
-            // levels 0..T-1 of this step (the input of each transposed sweep); a tile
-            // off the x/y faces only works when plane 1 or nz is among its levels
-            const bool zstep = (p0 >= 1 && p0 - (T - 1) <= 1) || (p0 >= g.nz && p0 - (T - 1) <= g.nz);
-            if (nxy > 0 || zstep) {
-                adj_faces(ring + SLOT * PLANE, 0, p0);
-#pragma unroll
-                for (int s = 1; s < T; ++s)
-                    if (m >= s) adj_faces(lvl + ((s - 1) * 2 + PAR) * PLANE, s, p0 - s);
-            }
-        }
         // the slot of plane Zlo+m-1 is free now: refill it with plane Zlo+m-1+NS,
         // and the rho ring's next slot with rho of the same k (see rho_slots)
         if (tid == 0 && m >= 1 && issued < M) {

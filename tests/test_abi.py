@@ -75,7 +75,7 @@ def test_max_depth_without_device(lib):
     want = {(_lib.JAC_F64, _lib.JAC_OP_SWEEP): 8, (_lib.JAC_F32, _lib.JAC_OP_SWEEP): 8,
             (_lib.JAC_BF16, _lib.JAC_OP_SWEEP): 8, (_lib.JAC_F32, _lib.JAC_OP_RHS): 6,
             (_lib.JAC_BF16, _lib.JAC_OP_RHS): 6, (_lib.JAC_F64, _lib.JAC_OP_RHS): 0,
-            (_lib.JAC_F32, _lib.JAC_OP_ADJOINT): 4, (_lib.JAC_F64, _lib.JAC_OP_ADJOINT): 4,
+            (_lib.JAC_F32, _lib.JAC_OP_ADJOINT): 8, (_lib.JAC_F64, _lib.JAC_OP_ADJOINT): 8,
             (_lib.JAC_BF16, _lib.JAC_OP_ADJOINT): 0}
     for (dt, op), mt in want.items():
         assert lib.jacobi_max_depth(dt, op) == mt, (dt, op)

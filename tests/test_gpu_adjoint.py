@@ -26,13 +26,15 @@ def _grad_gpu(x64, W, n, t, dtype, checkpoint=False):
 
 
 @pytest.mark.parametrize("dtype,tol", [("f64", 1e-13), ("f32", 2e-6)])
-def test_adjoint_matches_oracle_reverse_mode(dtype, tol):
-    nx, ny, nz, n = 23, 17, 13, 10
+@pytest.mark.parametrize("shape", [(23, 17, 13), (5, 30, 3)], ids=lambda s: "x".join(map(str, s)))
+def test_adjoint_matches_oracle_reverse_mode(dtype, tol, shape):
+    nx, ny, nz = shape
+    n = 10
     x = inputs.uniform_grid_f64(nx, ny, nz)
     W = inputs.normal_grid_f64(nx, ny, nz)
     want = oracle.grad_f64(W, n)
     scale = np.abs(want).max()
-    for t in (1, 2, 3, 4):
+    for t in (1, 2, 3, 4, 6, 8):
         got = _grad_gpu(x, W, n, t, dtype)
         assert np.abs(got - want).max() <= tol * scale, (t, np.abs(got - want).max())
 

@@ -35,14 +35,20 @@ def test_rhs_every_depth_matches_oracle(dtype, shape):
         assert np.array_equal(got, want), t
 
 
-def test_adjoint_same_bits_every_depth():
+@pytest.mark.parametrize("dtype", ["f32", "f64"])
+@pytest.mark.parametrize("shape", [(67, 70, 31), (9, 40, 2), (3, 2, 19)],
+                         ids=lambda s: "x".join(map(str, s)))
+def test_adjoint_same_bits_every_depth(dtype, shape):
+    """Adjoint sweeps at every depth give the bits of depth 1, the swept lambda and
+    the boundary gradient (face bands thicker than the grid included)."""
     import torch
     from paper_0912_4506_gb300 import api
-    nx, ny, nz, n = 67, 70, 31, 11
-    W = inputs.to_dtype(inputs.normal_grid_f64(nx, ny, nz), "f32", px=inputs.row_pitch(nx, "f32"))
+    nx, ny, nz = shape
+    n = 11
+    W = inputs.to_dtype(inputs.normal_grid_f64(nx, ny, nz), dtype, px=inputs.row_pitch(nx, dtype))
     res = {}
-    for t in (1, 2, 3, 4):
-        lam = api.as_grid(to_dev(W, "f32"), nx)
+    for t in range(1, 9):
+        lam = api.as_grid(to_dev(W, dtype), nx)
         lam[0] = 0
         lam[-1] = 0
         lam[:, 0] = 0
@@ -54,9 +60,9 @@ def test_adjoint_same_bits_every_depth():
         out = j.adjoint(gb, n, t)
         j.check()
         torch.cuda.synchronize()
-        res[t] = (to_host(out, "f32"), to_host(gb, "f32"))
+        res[t] = (to_host(out, dtype), to_host(gb, dtype))
         j.close()
-    for t in (2, 3, 4):
+    for t in range(2, 9):
         assert np.array_equal(res[t][0], res[1][0]), t
         assert np.array_equal(res[t][1], res[1][1]), t
 

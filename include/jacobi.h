@@ -208,17 +208,21 @@ JAC_API int jacobi_residual_accumulate(int nx, int ny, int nz, const double *u_i
  * result of n forward sweeps of Eq. 1).  The handle's grids hold the adjoint
  * field: A = lambda_n (W on the interior, zero boundary layer) on entry.  Each
  * sweep applies the transpose of one forward sweep, which is the same stencil on
- * a zero boundary, and every face cell b of the boundary layer receives
- * RN(1/6) * lambda_s at its interior neighbour: the blocked kernel stores those
- * values per sweep in a face buffer the handle owns (2*(ny*nz + nx*nz + nx*ny)
- * elements per sweep, allocated on the first call that needs more and kept until
- * jacobi_destroy; JAC_ENOMEM if that allocation fails), and one kernel at the end
- * of the call adds them into grad_bdry in sweep order (lambda_n's share first),
- * so the result is deterministic.  grad_bdry: a grid of the handle's layout and
- * dtype, pre-set by the caller (the direct term W on the boundary layer); only its
- * face cells are written.  After nsweeps the interior of the final grid is
- * dL/dA_0 and grad_bdry is dL/dg.  t as in jacobi_sweep (t = 0: depth 3 for
- * FP32, 1 for FP64; deepest 4).  dtype JAC_F32 or JAC_F64.
+ * a zero boundary (it runs on the plain sweep's blocked kernels), and every face
+ * cell b of the boundary layer receives RN(1/6) * lambda_s at its interior
+ * neighbour: per blocked pass, a band kernel recomputes the pass's levels along
+ * the six faces (bit-identical values) and stores them per sweep in a face buffer
+ * the handle owns (2*(ny*nz + nx*nz + nx*ny) elements per sweep, allocated on the
+ * first call that needs more and kept until jacobi_destroy; JAC_ENOMEM if that
+ * allocation fails); it runs on a second stream the handle creates on first use,
+ * ordered after the previous pass and before the next by events, so the call
+ * stays ordered on the handle's stream.  One kernel at the end of the call adds
+ * the rows into grad_bdry in sweep order (lambda_n's share first), so the result
+ * is deterministic.  grad_bdry: a grid of the handle's layout and dtype, pre-set
+ * by the caller (the direct term W on the boundary layer); only its face cells
+ * are written.  After nsweeps the interior of the final grid is dL/dA_0 and
+ * grad_bdry is dL/dg.  t as in jacobi_sweep (t = 0: depth 3 for FP32, 1 for
+ * FP64; deepest 8).  dtype JAC_F32 or JAC_F64.
  */
 JAC_API int jacobi_adjoint(jacobi_t h, void *grad_bdry, int nsweeps, int t,
                    int *final_is_b);

@@ -100,16 +100,20 @@ int run_wave(jacobi_s* h, int nsweeps, int t, int* final_is_b, jacobi_plan_info*
             }
         }
     }
+    // handle buffer: the done flags, the ticket and the abort word first (cleared
+    // once per call; pass p marks its flags with p + 1), the rings after them
     WavePlan wp[2];
-    size_t need = 0;
+    size_t flags = 0, rings = 0;
     for (int p = 0; p < 2; ++p) {
         const int d = p == 0 ? dp.t_full : dp.t_last;
         if (d == 0 || (p == 0 && dp.n_full == 0)) continue;
         if (!wave_plan(h->dtype, h->g, d, *we, h->device, h->num_sms, &wp[p]))
             return JAC_EUNSUPPORTED;
-        const size_t ring = (wp[p].ring_bytes + 255) & ~(size_t)255;
-        need = std::max(need, ring + wp[p].sync_ints * sizeof(int));
+        flags = std::max(flags, wp[p].flags);
+        rings = std::max(rings, wp[p].ring_bytes);
     }
+    const size_t sync_bytes = ((flags + 2) * sizeof(int) + 255) & ~(size_t)255;
+    const size_t need = sync_bytes + rings;
     if (info_only) {
         std::memset(info_only, 0, sizeof(*info_only));
         info_only->kernel = JAC_KERNEL_WAVE;
@@ -149,18 +153,20 @@ int run_wave(jacobi_s* h, int nsweeps, int t, int* final_is_b, jacobi_plan_info*
     // launch ends with the timeout status
     const char* hook = getenv("JACOBI_WAVE_TEST_MISSING_PRODUCER");
     const bool missing_producer = hook && hook[0] == '1';
+    int* sync = static_cast<int*>(h->wbuf);
+    if (cudaMemsetAsync(sync, 0, (flags + 2) * sizeof(int), h->stream) != cudaSuccess)
+        return JAC_ECUDA;
     int cur_b = 0;
     for (int p = 0; p < dp.passes(); ++p) {
         const WavePlan& w = p < dp.n_full ? wp[0] : wp[1];
-        const size_t ring = (w.ring_bytes + 255) & ~(size_t)255;
-        int* sync = reinterpret_cast<int*>(static_cast<char*>(h->wbuf) + ring);
-        if (cudaMemsetAsync(sync, 0, w.sync_ints * sizeof(int), h->stream) != cudaSuccess)
+        if (p > 0 &&
+            cudaMemsetAsync(sync + flags, 0, 2 * sizeof(int), h->stream) != cudaSuccess)
             return JAC_ECUDA;
         WaveArgs a;
         a.g = h->g;
         a.src = cur_b ? h->b : h->a;
         a.dst = h->inplace ? h->a : (cur_b ? h->a : h->b);
-        a.ring = h->wbuf;
+        a.ring = static_cast<char*>(h->wbuf) + sync_bytes;
         a.t = w.t;
         a.kb = w.kb;
         a.nb = w.nb;
@@ -172,8 +178,9 @@ int run_wave(jacobi_s* h, int nsweeps, int t, int* final_is_b, jacobi_plan_info*
         a.nitems = w.nitems;
         a.inplace = h->inplace;
         a.done = sync;
-        a.ticket = sync + (w.sync_ints - 2);
-        a.abort = sync + (w.sync_ints - 1);
+        a.epoch = p + 1;
+        a.ticket = sync + flags;
+        a.abort = sync + flags + 1;
         a.status = h->status;
         a.fast = fast;
         a.one = 1u;
@@ -199,7 +206,7 @@ int run_wave(jacobi_s* h, int nsweeps, int t, int* final_is_b, jacobi_plan_info*
             if (w.t >= 2) {
                 Geom gr = h->g;
                 gr.nz = (w.t - 1) * w.rp - 2;
-                if (!encode_grid_map(&map_ring, h->dtype, gr, h->wbuf, box_x, box_y))
+                if (!encode_grid_map(&map_ring, h->dtype, gr, a.ring, box_x, box_y))
                     return JAC_ECUDA;
             }
         }

@@ -308,7 +308,7 @@ bool wave_plan(int dtype, const Geom& g, int t, const WaveEntry& e, int device, 
                                      e.smem > (size_t)48 * 1024);
     w.ctas = (int)std::min<long long>(nitems, (long long)num_sms * occ);
     w.ring_bytes = (size_t)(t - 1) * (size_t)w.rp * plane_bytes;
-    w.sync_ints = (size_t)t * w.ntx * w.nty + 2;
+    w.flags = (size_t)t * w.ntx * w.nty * w.nb;
     *out = w;
     return true;
 }

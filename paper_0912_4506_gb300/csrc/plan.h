@@ -82,7 +82,7 @@ const WaveEntry* wave_for(int dtype);
 struct WavePlan {
     int t, kb, R, sk, rp, nb, ntx, nty, nitems, ctas;
     size_t ring_bytes;   // (t-1) * rp planes
-    size_t sync_ints;    // t * ntiles counters, the ticket and the abort flag
+    size_t flags;        // t * ntiles * nb done flags
 };
 bool wave_plan(int dtype, const Geom& g, int t, const WaveEntry& e, int device, int num_sms,
                WavePlan* out);

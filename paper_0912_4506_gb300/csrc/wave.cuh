@@ -14,13 +14,16 @@
 //    in the grid's layout), sized by the planner to stay in L2.  Level 0 is the
 //    source grid.  Level t is the destination grid, or the source itself for
 //    an in-place pass.
-//  * One counter per (level, tile) counts the blocks finished, in z order.  An
-//    item starts when three things hold.  Level s-1 of the 3 x 3 tile
-//    neighbourhood is done through block b+1: the lower distance of Eq. 3.
-//    Level s+1 of the neighbourhood has finished reading ring block b-R, whose
-//    slot this item overwrites: the upper distance of Eq. 3.  For an in-place
-//    pass (s = t), level 1 of the neighbourhood has read every value of the
-//    block that the item overwrites.
+//  * One flag per (level, tile, block) marks it done (the pass's epoch number,
+//    so no flag is ever cleared).  An item starts when three things hold.
+//    Blocks b-1 .. b+1 of level s-1 of the 3 x 3 tile neighbourhood are done:
+//    the lower distance of Eq. 3.  Level s+1 of the neighbourhood has finished
+//    reading ring block b-R, whose slot this item overwrites (its readers are
+//    blocks b-R-1 .. b-R+1): the upper distance of Eq. 3.  For an in-place pass
+//    (s = t), level 1 of the neighbourhood has read every value of the block that
+//    the item overwrites (blocks b-1 .. b+1 of level 1).  Counting blocks in z
+//    order instead would make a finished item wait for its tile's previous
+//    block before it could be marked.
 //  * Items are handed out by one atomic ticket in the order (b + sk s, s, tile)
 //    with a skew sk >= 1 and R > sk + 1.  In that order every item waits only
 //    for items with smaller tickets (its input, level s-1 of block b+1, comes
@@ -64,7 +67,8 @@ struct WaveArgs {
     int ntx, nty;     // tiles
     int nitems;       // t * nb * ntx * nty
     int inplace;
-    int* done;        // [t][ntx * nty] finished blocks per (level, tile)
+    int* done;        // [t][ntx * nty][nb]: == epoch once (level, tile, block) is done
+    int epoch;        // this pass's mark (a handle-wide pass count, from 1)
     int* ticket;      // next work item
     int* abort;       // set by a wait that ran out
     int* status;      // handle status word (kStatusTimeout)
@@ -325,58 +329,53 @@ __device__ __forceinline__ void wave_fail(const WaveArgs& a) {
 }
 
 // The start conditions of item (s, b, tile), watched by the control warp: lane
-// 9c + n watches condition c (0: level s-1 through block b+1; 1: level s+1
-// through block b-R+1, the readers of the ring slot overwritten; 2: level 1
-// through block b+1, in place) of neighbour n of the 3 x 3 tiles.  poll() reads
-// every counter once with relaxed loads; after it succeeds, one fence makes the
-// observation an acquire.
+// 9c + n watches condition c of neighbour n of the 3 x 3 tiles, three blocks
+// each: c = 0, the input: blocks b-1, b, b+1 of level s-1 (the planes k0-1 ..
+// k1+1 the item reads); c = 1, the readers of the ring slot overwritten: blocks
+// b-R-1 .. b-R+1 of level s+1; c = 2, in place: blocks b-1 .. b+1 of level 1,
+// the readers of the level-0 block overwritten.  poll() reads the flags once
+// with relaxed loads; after it succeeds, one fence makes the observation an
+// acquire.
 struct WaveDeps {
-    const int* ptr;
-    int target;
+    const int* ptr;  // flag of the first block watched
+    int nblk;        // blocks watched (0..3)
     __device__ __forceinline__ void init(const WaveArgs& a, int s, int b, int tile, int lane) {
         const int ntiles = a.ntx * a.nty;
         ptr = nullptr;
-        target = 0;
+        nblk = 0;
         if (lane < 27) {
             const int c = lane / 9, nn = lane % 9;
             const int x = tile % a.ntx + nn % 3 - 1, y = tile / a.ntx + nn / 3 - 1;
             if (x >= 0 && x < a.ntx && y >= 0 && y < a.nty) {
                 const int n = y * a.ntx + x;
+                int lev = 0, mid = 0;  // level (1..t) and middle block watched
                 if (c == 0 && s >= 2) {
-                    ptr = a.done + (s - 2) * ntiles + n;
-                    target = min(b + 2, a.nb);
+                    lev = s - 1;
+                    mid = b;
                 } else if (c == 1 && s < a.t && b >= a.R) {
-                    ptr = a.done + s * ntiles + n;
-                    target = min(b - a.R + 2, a.nb);
+                    lev = s + 1;
+                    mid = b - a.R;
                 } else if (c == 2 && s == a.t && a.inplace) {
-                    ptr = a.done + n;
-                    target = min(b + 2, a.nb);
+                    lev = 1;
+                    mid = b;
+                }
+                if (lev > 0) {
+                    const int b0 = max(mid - 1, 0), b1 = min(mid + 1, a.nb - 1);
+                    ptr = a.done + ((long long)(lev - 1) * ntiles + n) * a.nb + b0;
+                    nblk = b1 - b0 + 1;
                 }
             }
         }
     }
-    __device__ __forceinline__ bool poll() const {
-        const bool ok = ptr == nullptr || ld_relaxed(ptr) >= target;
+    // a flag never reverts within a pass: a lane whose blocks are done stops reading
+    __device__ __forceinline__ bool poll(int epoch) {
+        bool ok = true;
+        for (int i = 0; i < nblk; ++i) ok = ok && ld_relaxed(ptr + i) == epoch;
+        if (ok) nblk = 0;
         return __all_sync(0xffffffffu, ok);
     }
 };
 
-// Bounded wait of one thread for *c >= target (relaxed polling, then a fence).
-__device__ __forceinline__ bool wave_wait(const int* c, int target, const WaveArgs& a) {
-    if (ld_relaxed(c) < target) {
-        const uint64_t t0 = global_ns();
-        while (ld_relaxed(c) < target) {
-            if (ld_relaxed(a.abort) != 0) return false;
-            if (global_ns() - t0 > a.wait_ns) {
-                wave_fail(a);
-                return false;
-            }
-            __nanosleep(32);
-        }
-    }
-    __threadfence();
-    return true;
-}
 
 // Named barriers: "job i published" from the control warp to the compute warps,
 // one per job parity so that consecutive jobs never share a barrier generation.
@@ -633,14 +632,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 // Persistent kernel: each CTA takes tickets until the pass is done.  Warps
-// 0..WY-1 compute; warp WY is the control warp.  For job i the control warp
-// decodes the ticket and polls the job's start conditions; meanwhile it watches
-// job i-1 (still being computed) and releases it as soon as it is done, because
-// job i may depend on it.  Job i is published once its conditions hold and job
-// i-1 is done; if job i-1 is not yet released then, it is released right after.
-// So the checks of job i overlap the arithmetic of job i-1.  A CTA holds at most
-// two unreleased tickets and every wait is on a smaller ticket: the pass makes
-// progress for any number of CTAs.
+// 0..WY-1 compute; warp WY is the control warp.  The control warp decodes the
+// next ticket and polls that job's start conditions while the compute warps march
+// earlier jobs; it publishes a job as soon as its conditions hold, so the compute
+// warps find the next job waiting when they finish one.  At most two published
+// jobs are unreleased at a time: job j is published only after job j-2 is seen
+// done, which keeps the per-parity "job published" barriers and "job done"
+// mbarriers from ever holding two generations.  Finished jobs are released in
+// order from inside the same polling loop (a job may depend on the CTA's own
+// earlier job).  Every wait is on a smaller ticket, so the pass makes progress
+// for any number of CTAs.
 // TMA = 1: the compute warps use the TMA-staged march (FP32/bf16) with the maps
 // of the source grid and of the rings; TMA = 0: the register march (maps unused).
 template <class Tr, int V, int WY, int NEMU, int MINB, int TMA>
@@ -651,11 +652,12 @@ __global__ void __launch_bounds__(32 * (WY + 1), MINB)
     constexpr int kThreads = 32 * (WY + 1);
     extern __shared__ __align__(1024) unsigned char wsmem[];
     __shared__ int s_job[2][4];  // s, b, tile, go
-    __shared__ __align__(8) uint64_t s_done;
+    __shared__ __align__(8) uint64_t s_done[2];  // job j done: s_done[j & 1]
     const int lane = threadIdx.x;
     const int ntiles = a.ntx * a.nty;
     if (threadIdx.y == WY && lane == 0) {
-        mbar_init(&s_done, WY);
+        mbar_init(&s_done[0], WY);
+        mbar_init(&s_done[1], WY);
         if constexpr (TMA) {
             uint64_t* full = reinterpret_cast<uint64_t*>(wsmem);
             for (int i = 0; i < kWaveRing; ++i) mbar_init(&full[i], 1);
@@ -669,19 +671,42 @@ __global__ void __launch_bounds__(32 * (WY + 1), MINB)
     if (threadIdx.y == WY) {
         // ---- control warp
         int d = 1, base = 0;  // lane 0: diagonal b + sk s of the ticket, its first ticket
-        int it = 0;
+        int it = 0;           // lane 0: the next ticket
         if (lane == 0) it = atomicAdd(a.ticket, 1);
-        int prev_s = 0, prev_b = 0, prev_tile = 0;
-        auto release = [&](int s, int b, int tile) {
+        int js[2] = {0, 0}, jb[2] = {0, 0}, jt[2] = {0, 0};  // published jobs, by parity
+        int pub = 0, rel = 0;  // jobs < pub published, jobs < rel released
+        auto done = [&](int j) -> bool {  // job j computed (lane 0 reads, all agree)
+            int v = 0;
+            if (lane == 0) v = mbar_test(&s_done[j & 1], (uint32_t)((j >> 1) & 1)) ? 1 : 0;
+            return __shfl_sync(FULL, v, 0) != 0;
+        };
+        auto release = [&](int j) {  // the job's stores, then its flag
             if (lane == 0) {
-                int* c = a.done + (s - 1) * ntiles + tile;
+                int* f = a.done + ((long long)(js[j & 1] - 1) * ntiles + jt[j & 1]) * a.nb +
+                         jb[j & 1];
                 __threadfence();
-                if (wave_wait(c, b, a)) atomicAdd(c, 1);
+                atomicExch(f, a.epoch);
             }
             __syncwarp();
         };
+        auto publish = [&](int s, int b, int tile, int go) {
+            if (lane == 0) {
+                s_job[pub & 1][0] = s;
+                s_job[pub & 1][1] = b;
+                s_job[pub & 1][2] = tile;
+                s_job[pub & 1][3] = go;
+            }
+            js[pub & 1] = s;
+            jb[pub & 1] = b;
+            jt[pub & 1] = tile;
+            __syncwarp();
+            ready_arrive<kThreads>(pub);
+            ++pub;
+        };
+        bool failed = false;
 #pragma unroll 1
-        for (int i = 0;; ++i) {
+        while (true) {
+            // decode the next ticket
             int s = 0, b = 0, tile = 0;
             if (lane == 0 && it < a.nitems) {
                 while (true) {
@@ -706,19 +731,23 @@ __global__ void __launch_bounds__(32 * (WY + 1), MINB)
             tile = __shfl_sync(FULL, tile, 0);
             WaveDeps deps;
             deps.init(a, s, b, tile, lane);
-            bool deps_ok = !valid, prev_done = i == 0, prev_released = i == 0, failed = false;
-            const uint64_t t0 = lane == 0 ? global_ns() : 0;
+            bool deps_ok = !valid;
+            uint64_t t0 = lane == 0 ? global_ns() : 0;
 #pragma unroll 1
             while (true) {
+                bool progressed = false;
+                while (rel < pub && done(rel)) {
+                    release(rel);
+                    ++rel;
+                    progressed = true;
+                }
                 if (!deps_ok) {
-                    deps_ok = deps.poll();
+                    deps_ok = deps.poll(a.epoch);
                     if (deps_ok) __threadfence();  // acquire side of the counter polls
                 }
-                if (!prev_done) prev_done = mbar_test(&s_done, (uint32_t)((i - 1) & 1));
-                if (prev_done && deps_ok) break;
-                if (prev_done && !prev_released) {
-                    release(prev_s, prev_b, prev_tile);
-                    prev_released = true;
+                if (deps_ok && pub - rel < 2) break;
+                if (progressed) {
+                    if (lane == 0) t0 = global_ns();
                     continue;
                 }
                 int fail = 0;
@@ -734,23 +763,29 @@ __global__ void __launch_bounds__(32 * (WY + 1), MINB)
                     failed = true;
                     break;
                 }
-                __nanosleep(32);
+                __nanosleep(64);
             }
-            const int go = (valid && !failed) ? 1 : 0;
-            if (lane == 0) {
-                s_job[i & 1][0] = s;
-                s_job[i & 1][1] = b;
-                s_job[i & 1][2] = tile;
-                s_job[i & 1][3] = go;
-            }
-            __syncwarp();
-            ready_arrive<kThreads>(i);
-            if (lane == 0 && go) it = atomicAdd(a.ticket, 1);
-            if (!prev_released && !failed) release(prev_s, prev_b, prev_tile);
-            if (!go) break;
-            prev_s = s;
-            prev_b = b;
-            prev_tile = tile;
+            if (failed || !valid) break;
+            publish(s, b, tile, 1);
+            if (lane == 0) it = atomicAdd(a.ticket, 1);
+        }
+        // the stop job (go = 0) once at most one job is outstanding (jobs always
+        // finish: the compute warps' own waits are bounded), then the last
+        // releases; after a failed wait nothing more is released
+#pragma unroll 1
+        while (pub - rel >= 2) {
+            const uint64_t t1 = global_ns();
+            while (!done(rel) && global_ns() - t1 < a.wait_ns) __nanosleep(32);
+            if (!failed) release(rel);
+            ++rel;
+        }
+        publish(0, 0, 0, 0);
+#pragma unroll 1
+        while (rel < pub - 1) {
+            const uint64_t t1 = global_ns();
+            while (!done(rel) && global_ns() - t1 < a.wait_ns) __nanosleep(32);
+            if (!failed) release(rel);
+            ++rel;
         }
         return;
     }
@@ -773,7 +808,7 @@ __global__ void __launch_bounds__(32 * (WY + 1), MINB)
             wave_item<Tr, V, WY, NEMU>(a, s, b, tile, fast);
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&s_done);
+        if (lane == 0) mbar_arrive(&s_done[i & 1]);
     }
 }
 

@@ -153,8 +153,10 @@ template <class S>
 __global__ void __launch_bounds__(256) face_band_kernel(const S* __restrict__ src, const Geom g,
                                                         S* __restrict__ fbuf, long long fstride,
                                                         int sweep0, int T) {
+    // block (32, 8): thread (tu, tv) walks the band's cells with strides 32 and 8
     constexpr int TU = 32, TV = 8;
     extern __shared__ __align__(16) unsigned char band_smem[];
+    const int tu = threadIdx.x, tv = threadIdx.y;
     const int face = blockIdx.z;
     const int ax = face / 2;            // normal axis: 0 x, 1 y, 2 z
     const bool hi = (face & 1) != 0;    // face at the high end of the axis
@@ -174,68 +176,75 @@ __global__ void __launch_bounds__(256) face_band_kernel(const S* __restrict__ sr
                             : ax == 1 ? 2 * fxs + (face - 2) * fys
                                       : 2 * fxs + 2 * fys + (face - 4) * fzs;
     const int urow = ax == 0 ? g.ny : g.nx;  // face-buffer row length along u
+    // grid offsets of one step along u, along v and inward along the normal
+    const long long su = ax == 0 ? g.px : 1;
+    const long long sv = ax == 2 ? g.px : g.plane;
+    const long long sn_abs = ax == 0 ? 1 : ax == 1 ? g.px : g.plane;
+    const long long sn = hi ? -sn_abs : sn_abs;
+    const int w0 = hi ? nn : 1;  // the face layer along the normal
+    const long long origin = ax == 0 ? g.lin(w0, 0, 0) : ax == 1 ? g.lin(0, w0, 0)
+                                                                : g.lin(0, 0, w0);
 
     // level 0: band cell (n, iu, iv) is n layers in from the face, u = u0 - H + iu
-    // (unrolled so that a thread's loads are in flight together)
-#pragma unroll 8
-    for (int i = threadIdx.x; i < vol; i += blockDim.x) {
-        const int n = i / layer, r = i - n * layer, iv = r / BU, iu = r - iv * BU;
-        const int u = u0 - H + iu, v = v0 - H + iv;
-        S val = S(0);
-        if (n < nn && u >= 1 && u <= nu && v >= 1 && v <= nv) {
-            const int w = hi ? nn - n : 1 + n;
-            const int x = ax == 0 ? w : u, y = ax == 1 ? w : (ax == 0 ? u : v),
-                      z = ax == 2 ? w : v;
-            val = src[g.lin(x, y, z)];
+    for (int n = 0; n < T; ++n) {
+        const bool nin = n < nn;
+        for (int iv = tv; iv < BV; iv += TV) {
+            const int v = v0 - H + iv;
+            const bool vin = nin && v >= 1 && v <= nv;
+            for (int iu = tu; iu < BU; iu += TU) {
+                const int u = u0 - H + iu;
+                S val = S(0);
+                if (vin && u >= 1 && u <= nu) val = src[origin + n * sn + u * su + v * sv];
+                cur[n * layer + iv * BU + iu] = val;
+            }
         }
-        cur[i] = val;
     }
     __syncthreads();
     auto store_faces = [&](const S* lv, int s) {
+        const int u = u0 + tu, v = v0 + tv;
+        if (u > nu || v > nv) return;
+        const S lam = lv[(H + tv) * BU + (H + tu)];  // layer 0
         S* fb = fbuf + (long long)(sweep0 + s) * fstride + fbase;
-        for (int i = threadIdx.x; i < TU * TV; i += blockDim.x) {
-            const int du = i % TU, dv = i / TU;
-            const int u = u0 + du, v = v0 + dv;
-            if (u > nu || v > nv) continue;
-            const S lam = lv[(H + dv) * BU + (H + du)];  // layer 0
-            fb[(long long)(v - 1) * urow + (u - 1)] = sizeof(S) == 8
-                ? S(__dmul_rn((double)c6, (double)lam)) : S(__fmul_rn((float)c6, (float)lam));
-        }
+        fb[(long long)(v - 1) * urow + (u - 1)] = sizeof(S) == 8
+            ? S(__dmul_rn((double)c6, (double)lam)) : S(__fmul_rn((float)c6, (float)lam));
     };
     store_faces(cur, 0);
     for (int s = 1; s < T; ++s) {
         // level s on layers 0..T-1-s, within s cells less of halo
-        const int nl = T - s;
-        const int cu = BU - 2 * s, cv = BV - 2 * s;
-#pragma unroll 4
-        for (int i = threadIdx.x; i < nl * cu * cv; i += blockDim.x) {
-            const int n = i / (cu * cv), r = i - n * (cu * cv), jv = r / cu, ju = r - jv * cu;
-            const int iu = s + ju, iv = s + jv;
-            const int u = u0 - H + iu, v = v0 - H + iv;
-            const int c = n * layer + iv * BU + iu;
-            S out = S(0);
-            if (n < nn && u >= 1 && u <= nu && v >= 1 && v <= nv) {
-                // neighbours along the normal (n - 1 beyond the face is the boundary)
-                const S nlo = n > 0 ? cur[c - layer] : S(0), nhi = cur[c + layer];
-                const S along_m = hi ? nhi : nlo, along_p = hi ? nlo : nhi;  // -1, +1 of the axis
-                const S um = cur[c - 1], up = cur[c + 1], vm = cur[c - BU], vp = cur[c + BU];
-                S xm, xp, ym, yp, zm, zp;
-                if (ax == 0) { xm = along_m; xp = along_p; ym = um; yp = up; zm = vm; zp = vp; }
-                else if (ax == 1) { xm = um; xp = up; ym = along_m; yp = along_p; zm = vm; zp = vp; }
-                else { xm = um; xp = up; ym = vm; yp = vp; zm = along_m; zp = along_p; }
-                if constexpr (sizeof(S) == 8) {
-                    double a = __dadd_rn(xm, xp);
-                    a = __dadd_rn(a, ym); a = __dadd_rn(a, yp);
-                    a = __dadd_rn(a, zm); a = __dadd_rn(a, zp);
-                    out = __dmul_rn(a, (double)c6);
-                } else {
-                    float a = __fadd_rn(xm, xp);
-                    a = __fadd_rn(a, ym); a = __fadd_rn(a, yp);
-                    a = __fadd_rn(a, zm); a = __fadd_rn(a, zp);
-                    out = __fmul_rn(a, (float)c6);
+        for (int n = 0; n < T - s; ++n) {
+            const bool nin = n < nn;
+            for (int iv = s + tv; iv < BV - s; iv += TV) {
+                const int v = v0 - H + iv;
+                const bool vin = nin && v >= 1 && v <= nv;
+                for (int iu = s + tu; iu < BU - s; iu += TU) {
+                    const int u = u0 - H + iu;
+                    const int c = n * layer + iv * BU + iu;
+                    S out = S(0);
+                    if (vin && u >= 1 && u <= nu) {
+                        // neighbours along the normal (n - 1 beyond the face is the boundary)
+                        const S nlo = n > 0 ? cur[c - layer] : S(0), nhi = cur[c + layer];
+                        const S am = hi ? nhi : nlo, ap = hi ? nlo : nhi;  // axis -1, +1
+                        const S um = cur[c - 1], up = cur[c + 1];
+                        const S vm = cur[c - BU], vp = cur[c + BU];
+                        S xm, xp, ym, yp, zm, zp;
+                        if (ax == 0) { xm = am; xp = ap; ym = um; yp = up; zm = vm; zp = vp; }
+                        else if (ax == 1) { xm = um; xp = up; ym = am; yp = ap; zm = vm; zp = vp; }
+                        else { xm = um; xp = up; ym = vm; yp = vp; zm = am; zp = ap; }
+                        if constexpr (sizeof(S) == 8) {
+                            double acc = __dadd_rn(xm, xp);
+                            acc = __dadd_rn(acc, ym); acc = __dadd_rn(acc, yp);
+                            acc = __dadd_rn(acc, zm); acc = __dadd_rn(acc, zp);
+                            out = __dmul_rn(acc, (double)c6);
+                        } else {
+                            float acc = __fadd_rn(xm, xp);
+                            acc = __fadd_rn(acc, ym); acc = __fadd_rn(acc, yp);
+                            acc = __fadd_rn(acc, zm); acc = __fadd_rn(acc, zp);
+                            out = __fmul_rn(acc, (float)c6);
+                        }
+                    }
+                    nxt[c] = out;
                 }
             }
-            nxt[c] = out;
         }
         __syncthreads();
         store_faces(nxt, s);
@@ -257,14 +266,14 @@ cudaError_t launch_face_band(int dtype, const void* src, const Geom& g, void* fb
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(face_band_kernel<double>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        face_band_kernel<double><<<grid, 256, smem, st>>>(static_cast<const double*>(src), g,
+        face_band_kernel<double><<<grid, dim3(32, 8), smem, st>>>(static_cast<const double*>(src), g,
                                                           static_cast<double*>(fbuf), fstride,
                                                           sweep0, T);
     } else {
         if (smem > 48 * 1024)
             cudaFuncSetAttribute(face_band_kernel<float>,
                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        face_band_kernel<float><<<grid, 256, smem, st>>>(static_cast<const float*>(src), g,
+        face_band_kernel<float><<<grid, dim3(32, 8), smem, st>>>(static_cast<const float*>(src), g,
                                                          static_cast<float*>(fbuf), fstride,
                                                          sweep0, T);
     }

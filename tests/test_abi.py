@@ -59,6 +59,14 @@ def test_create_rejects_bad_arguments_without_device(lib):
         assert rc == _lib.JAC_EINVAL, (nx, ny, nz, dt, pitch, rc)
     assert lib.jacobi_sweep(None, 1, 0, None) == _lib.JAC_EINVAL
     assert lib.jacobi_destroy(None) == _lib.JAC_OK
+    # a two-grid handle needs B; the one-grid handle the same checks on its grid
+    assert lib.jacobi_create(ctypes.byref(h), 4, 4, 4, 0, P(16), P(0), 6, None) == _lib.JAC_EINVAL
+    for nx, ny, nz, dt, a, pitch in [(0, 4, 4, 0, P(16), 8), (4, 4, 4, 7, P(16), 8),
+                                     (4, 4, 4, 0, P(16), 5), (4, 4, 4, 0, P(0), 6),
+                                     (4, 4, 4, 0, P(17), 6), (4, 4, 4, 1, P(16), 6)]:
+        rc = lib.jacobi_create_inplace(ctypes.byref(h), nx, ny, nz, dt, a, pitch, None)
+        assert rc == _lib.JAC_EINVAL, (nx, ny, nz, dt, pitch, rc)
+    assert lib.jacobi_create_inplace(None, 4, 4, 4, 0, P(16), 6, None) == _lib.JAC_EINVAL
 
 
 def test_missing_library_fails_loudly(tmp_path):

@@ -211,7 +211,10 @@ __device__ __forceinline__ void plain_march_acc(const double* __restrict__ A,
     double dn[V], ct[V], up[V], no[V], so[V];
     load(pa - plane, dn);
     load(pa, ct);
-#pragma unroll 1
+    // two planes per iteration: the two planes' integer-pipe chains interleave
+    // (512^3: 208.9 GLUP/s against 201.9 with one plane per iteration, at the same
+    // 48 registers)
+#pragma unroll 2
     for (int k = k0; k <= k1; ++k) {
         load(pa + plane, up);
         load(pa - px, no);

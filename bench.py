@@ -40,8 +40,8 @@ ALGO_BYTES_PER_LUP = {"f64": 16, "f32": 8, "bf16": 4}
 # to 512^3 by the lattice-site updates (traffic is proportional to them: 16 B per
 # update, no re-reads).  A kernel without a capture of its current code: None.
 TRAFFIC_PER_LAUNCH = {
-    # 482.2 MB read + 408.7 MB written for 384^3 (56.6 M updates)
-    "plain_sweep_kernel<F64,emu=8>": round((482179072 + 408687872) * (512 / 384) ** 3),
+    # 484.4 MB read + 409.7 MB written for 384^3 (56.6 M updates)
+    "plain_sweep_kernel<F64,emu=8>": round((484390912 + 409657088) * (512 / 384) ** 3),
 }
 
 # Instructions per computed cell update of the blocked kernels, read from ncu

@@ -76,6 +76,8 @@ def parse():
     p.add_argument("--kernel", default="auto", choices=["auto", "plain", "tb", "wave"])
     p.add_argument("--size", type=int, default=NX)
     p.add_argument("--sweeps", type=int, default=NSWEEPS)
+    p.add_argument("--slabs", action="store_true",
+                   help="run the z-slab decomposition also at N = 1 (one slab, no exchange)")
     p.add_argument("--replicas", action="store_true",
                    help="N > 1: independent 512^3 grids per rank (no halo exchange) instead "
                         "of the z-slab decomposition of one 512 x 512 x 512N grid")
@@ -564,7 +566,7 @@ def run_ours(args):
     # with their neighbours by NCCL send/recv, then sweep their slab (core plus
     # halos) with the library's FP64 choice.  --replicas: independent grids.
     rs = None
-    if world > 1 and not args.replicas:
+    if (world > 1 or args.slabs) and not args.replicas:
         from paper_0912_4506_gb300 import inputs, slabs
         nzg = NZ * world
         z0, z1 = slabs.slab_ranges(nzg, world)[rank]
@@ -577,7 +579,7 @@ def run_ours(args):
         npasses = len(rs.passes(NSWEEPS, SLAB_H))
         launches_per_step = NSWEEPS if kt == 1 else sum(
             -(-d // min(kt, d)) for d in rs.passes(NSWEEPS, SLAB_H))
-        range_checks_per_step *= npasses
+        range_checks_per_step *= npasses if world > 1 else 1  # one call at one rank
 
     def step():
         if rs is not None:
@@ -641,7 +643,7 @@ def run_ours(args):
         # every step: this rank's slab from pinned host memory, the decomposed
         # sweeps, this rank's core planes back to the host
         host_in = torch.from_numpy(a_slab).pin_memory()
-        host_out = torch.empty_like(rs.core()).pin_memory()
+        host_out = torch.empty_like(rs.core(), device="cpu").pin_memory()
         e2 = torch.cuda.Event(enable_timing=True)
         e3 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
@@ -708,7 +710,8 @@ def run_ours(args):
                    else f"jacobi7pt_512x512x{NZ * world}_fp64_100sweeps_zslabs",
                    "nx": NX, "ny": NY, "nz": NZ if rs is None else NZ * world,
                    "sweeps_per_step": NSWEEPS, "plan": plan,
-                   "parallelism": ("single" if world == 1 else "replicas" if rs is None
+                   "parallelism": ("single" if rs is None and world == 1
+                                   else "replicas" if rs is None
                                    else f"z-slabs x {world}, {SLAB_H}-plane halos by NCCL "
                                         f"send/recv every {SLAB_H} sweeps"),
                    "l2": "inputs larger than L2 (1.09 GB per grid), no flush"},

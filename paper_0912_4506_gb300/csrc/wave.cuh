@@ -14,8 +14,9 @@
 //    in the grid's layout), sized by the planner to stay in L2.  Level 0 is the
 //    source grid.  Level t is the destination grid, or the source itself for
 //    an in-place pass.
-//  * One flag per (level, tile, block) marks it done (the pass's epoch number,
-//    so no flag is ever cleared).  An item starts when three things hold.
+//  * One flag per (level, tile, block) marks it done (with the pass's number in
+//    the call, so the flags are cleared once per call, not per pass).  An item
+//    starts when three things hold.
 //    Blocks b-1 .. b+1 of level s-1 of the 3 x 3 tile neighbourhood are done:
 //    the lower distance of Eq. 3.  Level s+1 of the neighbourhood has finished
 //    reading ring block b-R, whose slot this item overwrites (its readers are
@@ -68,7 +69,7 @@ struct WaveArgs {
     int nitems;       // t * nb * ntx * nty
     int inplace;
     int* done;        // [t][ntx * nty][nb]: == epoch once (level, tile, block) is done
-    int epoch;        // this pass's mark (a handle-wide pass count, from 1)
+    int epoch;        // this pass's mark: its index in the call + 1 (flags cleared per call)
     int* ticket;      // next work item
     int* abort;       // set by a wait that ran out
     int* status;      // handle status word (kStatusTimeout)

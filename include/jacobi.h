@@ -157,7 +157,7 @@ JAC_API int jacobi_sweep(jacobi_t h, int nsweeps, int t, int *final_is_b);
  * the items that still read the buffer it overwrites are done, as the paper's
  * per-thread counters pace its team.  Updates 1..t-1 of a pass live in ring
  * buffers that the handle allocates on first use (kept until destroy, grown when
- * a deeper pass needs more; sized to stay in L2), so no cell is recomputed and
+ * a deeper pass needs more; 512 MB at most), so no cell is recomputed and
  * each pass reads and writes the grid once.  Every wait on another item is
  * bounded (2 s); a wait that runs out ends the launch, and jacobi_check returns
  * JAC_ETIMEOUT.  Results are bit-identical to the other kernels.  For failure-

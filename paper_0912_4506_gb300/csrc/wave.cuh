@@ -11,7 +11,8 @@
 //  * A work item is one level s (1..t) of one block.  A block is an x-y tile of
 //    32V x WY cells (one warp per row, V cells per lane) and kb planes in z.
 //  * Levels 1..t-1 live in ring buffers of rp planes each (rp = R kb, full planes
-//    in the grid's layout), sized by the planner to stay in L2.  Level 0 is the
+//    in the grid's layout), 512 MB at most (the planner's budget; larger items
+//    measured faster than rings held to the L2 size).  Level 0 is the
 //    source grid.  Level t is the destination grid, or the source itself for
 //    an in-place pass.
 //  * One flag per (level, tile, block) marks it done (with the pass's number in

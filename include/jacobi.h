@@ -208,9 +208,10 @@ JAC_API int jacobi_residual_accumulate(int nx, int ny, int nz, const double *u_i
  * result of n forward sweeps of Eq. 1).  The handle's grids hold the adjoint
  * field: A = lambda_n (W on the interior, zero boundary layer) on entry.  Each
  * sweep applies the transpose of one forward sweep, which is the same stencil on
- * a zero boundary (it runs on the plain sweep's blocked kernels), and every face
+ * a zero boundary (it runs on the plain sweep's kernels: the streaming kernel for
+ * FP64 at depth 1, the blocked kernels otherwise), and every face
  * cell b of the boundary layer receives RN(1/6) * lambda_s at its interior
- * neighbour: per blocked pass, a band kernel recomputes the pass's levels along
+ * neighbour: per pass, a band kernel recomputes the pass's levels along
  * the six faces (bit-identical values) and stores them per sweep in a face buffer
  * the handle owns (2*(ny*nz + nx*nz + nx*ny) elements per sweep, allocated on the
  * first call that needs more and kept until jacobi_destroy; JAC_ENOMEM if that

@@ -240,8 +240,38 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
     // (128 x 12 tiles), which keeps more bytes in flight than the register march
     if (kernel == JAC_KERNEL_AUTO)
         kernel = (t == 1 && h->dtype == JAC_F64) ? JAC_KERNEL_PLAIN : JAC_KERNEL_TB;
-    if (mode != MODE_PLAIN) kernel = JAC_KERNEL_TB;  // RHS/adjoint only exist blocked
+    if (mode == MODE_RHS) kernel = JAC_KERNEL_TB;  // correction sweeps only exist blocked
     if (cudaSetDevice(h->device) != cudaSuccess) return JAC_ECUDA;
+
+    // adjoint: one row of face values per sweep, added to the gradient at the end;
+    // the face bands run on a side stream beside the sweeps
+    const long long fstride = 2LL * ((long long)h->g.ny * h->g.nz +
+                                     (long long)h->g.nx * h->g.nz +
+                                     (long long)h->g.nx * h->g.ny);
+    if (mode == MODE_ADJ && nsweeps > 0 && !info_only) {
+        const size_t need = (size_t)fstride * (size_t)nsweeps * (size_t)elem_size(h->dtype);
+        const int grc = grow_buffer(h, &h->fbuf, &h->fbuf_bytes, need);
+        if (grc != JAC_OK) return grc;
+        if (!h->side) {
+            if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_band, cudaEventDisableTiming) != cudaSuccess)
+                return JAC_ECUDA;
+        }
+    }
+    // the face values of the levels 0..T-1 of a pass come from its input (the band
+    // kernel on the side stream, beside the pass, which only reads the same input);
+    // the next pass, which overwrites that input, waits for it
+    auto band_before = [&](const void* src, int sweep0, int T) -> bool {
+        return cudaEventRecord(h->ev_in, h->stream) == cudaSuccess &&
+               cudaStreamWaitEvent(h->side, h->ev_in, 0) == cudaSuccess &&
+               launch_face_band(h->dtype, src, h->g, h->fbuf, fstride, sweep0, T, h->side) ==
+                   cudaSuccess &&
+               cudaEventRecord(h->ev_band, h->side) == cudaSuccess;
+    };
+    auto band_after = [&]() -> bool {
+        return cudaStreamWaitEvent(h->stream, h->ev_band, 0) == cudaSuccess;
+    };
 
     if (kernel == JAC_KERNEL_PLAIN) {
         const PlainEntry* pe = plain_for(h->dtype);
@@ -276,9 +306,15 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         for (int s = 0; s < nsweeps; ++s) {
             const void* src = (s & 1) ? h->b : h->a;
             void* dst = (s & 1) ? h->a : h->b;
+            if (mode == MODE_ADJ && !band_before(src, s, 1)) return JAC_ECUDA;
             if (pe->launch(src, dst, h->g, kchunk, grid, fast, h->stream) != cudaSuccess)
                 return JAC_ECUDA;
+            if (mode == MODE_ADJ && !band_after()) return JAC_ECUDA;
         }
+        if (mode == MODE_ADJ && nsweeps > 0 &&
+            launch_face_reduce(h->dtype, grad, h->g, h->fbuf, fstride, nsweeps, h->stream) !=
+                cudaSuccess)
+            return JAC_ECUDA;
         if (final_is_b) *final_is_b = nsweeps & 1;
         return JAC_OK;
     }
@@ -336,36 +372,12 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         }
     }
 
-    // adjoint: one row of face values per sweep, added to the gradient at the end
-    const long long fstride = 2LL * ((long long)h->g.ny * h->g.nz +
-                                     (long long)h->g.nx * h->g.nz +
-                                     (long long)h->g.nx * h->g.ny);
-    if (mode == MODE_ADJ && nsweeps > 0) {
-        const size_t need = (size_t)fstride * (size_t)nsweeps * (size_t)elem_size(h->dtype);
-        const int grc = grow_buffer(h, &h->fbuf, &h->fbuf_bytes, need);
-        if (grc != JAC_OK) return grc;
-        if (!h->side) {
-            if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&h->ev_band, cudaEventDisableTiming) != cudaSuccess)
-                return JAC_ECUDA;
-        }
-    }
-
     int cur_b = 0;  // 0: current data in A
     int sweep0 = 0;
     for (int p = 0; p < dp.passes(); ++p) {
         const TBEntry* e = tb_entry(h->dtype, kmode, dp.depth(p));
         if (!e) return JAC_EUNSUPPORTED;
-        // adjoint: the face values of this pass's levels come from its input; the band
-        // kernel runs on the side stream beside the pass (both only read the input),
-        // and the next pass, which overwrites that input, waits for it
-        if (mode == MODE_ADJ &&
-            (cudaEventRecord(h->ev_in, h->stream) != cudaSuccess ||
-             cudaStreamWaitEvent(h->side, h->ev_in, 0) != cudaSuccess ||
-             launch_face_band(h->dtype, cur_b ? h->b : h->a, h->g, h->fbuf, fstride, sweep0,
-                              e->T, h->side) != cudaSuccess ||
-             cudaEventRecord(h->ev_band, h->side) != cudaSuccess))
+        if (mode == MODE_ADJ && !band_before(cur_b ? h->b : h->a, sweep0, e->T))
             return JAC_ECUDA;
         const TileGeom gm = tile_geom(h->dtype, h->g, e->V, e->NW, e->T,
                                       slots_per_sm * tb_occupancy(*e, h->device), 0);
@@ -400,8 +412,7 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         if (e->launch(map, map_rho, args, dim3(gm.ntx, gm.nty, gm.nchunk), h->stream) !=
             cudaSuccess)
             return JAC_ECUDA;
-        if (mode == MODE_ADJ && cudaStreamWaitEvent(h->stream, h->ev_band, 0) != cudaSuccess)
-            return JAC_ECUDA;
+        if (mode == MODE_ADJ && !band_after()) return JAC_ECUDA;
         cur_b ^= 1;
         sweep0 += e->T;
     }
@@ -496,8 +507,8 @@ int jacobi_adjoint(jacobi_t h, void* grad_bdry, int nsweeps, int t, int* final_i
     if (!h || !grad_bdry || !aligned16(grad_bdry)) return JAC_EINVAL;
     if (h->dtype == JAC_BF16) return JAC_EUNSUPPORTED;
     if (grad_bdry == h->a || grad_bdry == h->b) return JAC_EINVAL;
-    return run_passes(h, MODE_ADJ, nsweeps, t, JAC_KERNEL_TB, nullptr, grad_bdry, final_is_b,
-                      nullptr);
+    return run_passes(h, MODE_ADJ, nsweeps, t, JAC_KERNEL_AUTO, nullptr, grad_bdry,
+                      final_is_b, nullptr);
 }
 
 int jacobi_residual_accumulate(int nx, int ny, int nz, const double* u_in, double* u_out,

@@ -413,7 +413,9 @@ __device__ __forceinline__ void ready_arrive(int i) {
 // an 8-slot ring refilled two steps late, measured slower: FP32 558 / 446 GLUP/s
 // at t = 1 / 4 against 606 / 484; the barrier's stall is mostly the slowest
 // warp's copy.)
-constexpr int kWaveRing = 6;
+// 8 slots: 4 CTAs per SM in shared memory; against 6, bf16 +5 % and FP32 +3 % at
+// depth 4 (512^3); 10 slots measured slower
+constexpr int kWaveRing = 8;
 constexpr int kBarStep = 3;  // named barrier among the compute warps
 
 template <class S, int V, int WY>

@@ -215,9 +215,14 @@ JAC_API int jacobi_residual_accumulate(int nx, int ny, int nz, const double *u_i
  * the six faces (bit-identical values) and stores them per sweep in a face buffer
  * the handle owns (2*(ny*nz + nx*nz + nx*ny) elements per sweep, allocated on the
  * first call that needs more and kept until jacobi_destroy; JAC_ENOMEM if that
- * allocation fails); it runs on a second stream the handle creates on first use,
- * ordered after the previous pass and before the next by events, so the call
- * stays ordered on the handle's stream.  One kernel at the end of the call adds
+ * allocation fails); it runs on a second stream the handle creates on first use.
+ * So that a band can run beside the next pass as well, the passes rotate through
+ * A, B and a third grid of the same layout that the handle owns (allocated on
+ * the first adjoint call, given A's boundary layer at every call, freed by
+ * jacobi_destroy; JAC_ENOMEM if that allocation fails): a pass waits, by an
+ * event, only for the band that read the grid it writes, the call stays ordered
+ * on the handle's stream, and the last pass writes A or B (final_is_b says
+ * which; the other grids' contents are unspecified).  One kernel at the end of the call adds
  * the rows into grad_bdry in sweep order (lambda_n's share first), so the result
  * is deterministic.  grad_bdry: a grid of the handle's layout and dtype, pre-set
  * by the caller (the direct term W on the boundary layer); only its face cells

@@ -37,7 +37,11 @@ struct jacobi_s {
     void* fbuf;           // adjoint: face values per sweep (owned, grown on demand)
     size_t fbuf_bytes;
     cudaStream_t side;    // adjoint: face bands run beside the passes (created on first use)
-    cudaEvent_t ev_in, ev_band;
+    cudaEvent_t ev_in, ev_band[3];  // ev_band[i]: last band that read grid i (A, B, C)
+    void* c;              // adjoint: third grid of the rotation (owned, grown on demand)
+    size_t c_bytes;
+    CUtensorMap map_c;
+    int map_c_box_x, map_c_box_y;
     int inplace;          // one grid (jacobi_create_inplace): b == nullptr
     void* wbuf;           // pipelined passes: rings and counters (owned, grown on demand)
     size_t wbuf_bytes;
@@ -250,27 +254,61 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
                                      (long long)h->g.nx * h->g.ny);
     if (mode == MODE_ADJ && nsweeps > 0 && !info_only) {
         const size_t need = (size_t)fstride * (size_t)nsweeps * (size_t)elem_size(h->dtype);
-        const int grc = grow_buffer(h, &h->fbuf, &h->fbuf_bytes, need);
+        int grc = grow_buffer(h, &h->fbuf, &h->fbuf_bytes, need);
         if (grc != JAC_OK) return grc;
+        void* old_c = h->c;
+        const size_t grid_bytes = (size_t)h->g.plane * (size_t)(h->g.nz + 2) *
+                                  (size_t)elem_size(h->dtype);
+        grc = grow_buffer(h, &h->c, &h->c_bytes, grid_bytes);
+        if (grc != JAC_OK) return grc;
+        if (h->c != old_c) h->map_c_box_x = h->map_c_box_y = 0;  // stale descriptor
         if (!h->side) {
             if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&h->ev_band, cudaEventDisableTiming) != cudaSuccess)
+                cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming) != cudaSuccess)
                 return JAC_ECUDA;
+            for (int i = 0; i < 3; ++i)
+                if (cudaEventCreateWithFlags(&h->ev_band[i], cudaEventDisableTiming) !=
+                    cudaSuccess)
+                    return JAC_ECUDA;
         }
+        // the third grid carries A's boundary layer like B
+        if (launch_boundary_copy(h->dtype, h->a, h->c, h->g, h->stream) != cudaSuccess)
+            return JAC_ECUDA;
     }
-    // the face values of the levels 0..T-1 of a pass come from its input (the band
-    // kernel on the side stream, beside the pass, which only reads the same input);
-    // the next pass, which overwrites that input, waits for it
-    auto band_before = [&](const void* src, int sweep0, int T) -> bool {
+    // Adjoint grids rotate through A, B and C: the face values of the levels
+    // 0..T-1 of a pass come from its input (the band kernel on the side stream,
+    // beside the pass, which only reads the same input), and a pass writes to the
+    // grid that is neither its input nor the previous pass's input, so it waits
+    // only for the band of the pass before last (the one that read its output
+    // grid).  The last pass writes to A or B.  Other modes alternate A and B.
+    void* const grids[3] = {h->a, h->b, h->c};
+    bool band_pending[3] = {false, false, false};
+    int cur = 0, prev = -1;  // grid of the current input, of the previous input
+    auto band_before = [&](int sweep0, int T) -> bool {
+        band_pending[cur] = true;
         return cudaEventRecord(h->ev_in, h->stream) == cudaSuccess &&
                cudaStreamWaitEvent(h->side, h->ev_in, 0) == cudaSuccess &&
-               launch_face_band(h->dtype, src, h->g, h->fbuf, fstride, sweep0, T, h->side) ==
-                   cudaSuccess &&
-               cudaEventRecord(h->ev_band, h->side) == cudaSuccess;
+               launch_face_band(h->dtype, grids[cur], h->g, h->fbuf, fstride, sweep0, T,
+                                h->side) == cudaSuccess &&
+               cudaEventRecord(h->ev_band[cur], h->side) == cudaSuccess;
     };
-    auto band_after = [&]() -> bool {
-        return cudaStreamWaitEvent(h->stream, h->ev_band, 0) == cudaSuccess;
+    auto band_wait = [&](int i) -> bool {
+        if (!band_pending[i]) return true;
+        band_pending[i] = false;
+        return cudaStreamWaitEvent(h->stream, h->ev_band[i], 0) == cudaSuccess;
+    };
+    // the grid the next pass writes (waiting for a band still reading it)
+    auto next_grid = [&](bool last) -> int {
+        if (mode != MODE_ADJ) return cur ^ 1;
+        int d = prev < 0 ? 1 : 3 - cur - prev;
+        if (last && d == 2) d = prev;
+        return d;
+    };
+    // all bands done, then the face rows into the gradient
+    auto finish_adjoint = [&]() -> bool {
+        return band_wait(0) && band_wait(1) && band_wait(2) &&
+               launch_face_reduce(h->dtype, grad, h->g, h->fbuf, fstride, nsweeps,
+                                  h->stream) == cudaSuccess;
     };
 
     if (kernel == JAC_KERNEL_PLAIN) {
@@ -304,18 +342,17 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
                 return JAC_ECUDA;
         }
         for (int s = 0; s < nsweeps; ++s) {
-            const void* src = (s & 1) ? h->b : h->a;
-            void* dst = (s & 1) ? h->a : h->b;
-            if (mode == MODE_ADJ && !band_before(src, s, 1)) return JAC_ECUDA;
-            if (pe->launch(src, dst, h->g, kchunk, grid, fast, h->stream) != cudaSuccess)
-                return JAC_ECUDA;
-            if (mode == MODE_ADJ && !band_after()) return JAC_ECUDA;
-        }
-        if (mode == MODE_ADJ && nsweeps > 0 &&
-            launch_face_reduce(h->dtype, grad, h->g, h->fbuf, fstride, nsweeps, h->stream) !=
+            if (mode == MODE_ADJ && !band_before(s, 1)) return JAC_ECUDA;
+            const int dst = next_grid(s + 1 == nsweeps);
+            if (!band_wait(dst)) return JAC_ECUDA;
+            if (pe->launch(grids[cur], grids[dst], h->g, kchunk, grid, fast, h->stream) !=
                 cudaSuccess)
-            return JAC_ECUDA;
-        if (final_is_b) *final_is_b = nsweeps & 1;
+                return JAC_ECUDA;
+            prev = cur;
+            cur = dst;
+        }
+        if (mode == MODE_ADJ && nsweeps > 0 && !finish_adjoint()) return JAC_ECUDA;
+        if (final_is_b) *final_is_b = cur;
         return JAC_OK;
     }
 
@@ -372,13 +409,11 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
         }
     }
 
-    int cur_b = 0;  // 0: current data in A
     int sweep0 = 0;
     for (int p = 0; p < dp.passes(); ++p) {
         const TBEntry* e = tb_entry(h->dtype, kmode, dp.depth(p));
         if (!e) return JAC_EUNSUPPORTED;
-        if (mode == MODE_ADJ && !band_before(cur_b ? h->b : h->a, sweep0, e->T))
-            return JAC_ECUDA;
+        if (mode == MODE_ADJ && !band_before(sweep0, e->T)) return JAC_ECUDA;
         const TileGeom gm = tile_geom(h->dtype, h->g, e->V, e->NW, e->T,
                                       slots_per_sm * tb_occupancy(*e, h->device), 0);
         if (!gm.ok) return JAC_EUNSUPPORTED;
@@ -390,9 +425,16 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
             h->map_box_x = EX;
             h->map_box_y = EY;
         }
+        if (cur == 2 && (EX != h->map_c_box_x || EY != h->map_c_box_y)) {
+            if (!encode_grid_map(&h->map_c, h->dtype, h->g, h->c, EX, EY)) return JAC_ECUDA;
+            h->map_c_box_x = EX;
+            h->map_c_box_y = EY;
+        }
+        const int dst = next_grid(p + 1 == dp.passes());
+        if (!band_wait(dst)) return JAC_ECUDA;
         TBArgs args;
         args.g = h->g;
-        args.dst = cur_b ? h->a : h->b;
+        args.dst = grids[dst];
         args.grad = grad;
         args.ox = gm.ox;
         args.x0_first = gm.x0_first;
@@ -407,20 +449,17 @@ int run_passes(jacobi_s* h, int mode, int nsweeps, int t, int kernel, const void
             h->rho_box_x = EX;
             h->rho_box_y = EY;
         }
-        const CUtensorMap& map = cur_b ? h->map_b : h->map_a;
+        const CUtensorMap& map = cur == 0 ? h->map_a : cur == 1 ? h->map_b : h->map_c;
         const CUtensorMap& map_rho = mode == MODE_RHS ? h->map_rho : map;
         if (e->launch(map, map_rho, args, dim3(gm.ntx, gm.nty, gm.nchunk), h->stream) !=
             cudaSuccess)
             return JAC_ECUDA;
-        if (mode == MODE_ADJ && !band_after()) return JAC_ECUDA;
-        cur_b ^= 1;
+        prev = cur;
+        cur = dst;
         sweep0 += e->T;
     }
-    if (mode == MODE_ADJ && nsweeps > 0 &&
-        launch_face_reduce(h->dtype, grad, h->g, h->fbuf, fstride, nsweeps, h->stream) !=
-            cudaSuccess)
-        return JAC_ECUDA;
-    if (final_is_b) *final_is_b = cur_b;
+    if (mode == MODE_ADJ && nsweeps > 0 && !finish_adjoint()) return JAC_ECUDA;
+    if (final_is_b) *final_is_b = cur;
     return JAC_OK;
 }
 
@@ -585,11 +624,12 @@ int jacobi_destroy(jacobi_t h) {
     cudaStreamSynchronize(h->stream);
     cudaFree(h->status);
     if (h->fbuf) cudaFree(h->fbuf);
+    if (h->c) cudaFree(h->c);
     if (h->wbuf) cudaFree(h->wbuf);
     if (h->side) {
         cudaStreamSynchronize(h->side);
         cudaEventDestroy(h->ev_in);
-        cudaEventDestroy(h->ev_band);
+        for (int i = 0; i < 3; ++i) cudaEventDestroy(h->ev_band[i]);
         cudaStreamDestroy(h->side);
     }
     delete h;

@@ -138,148 +138,6 @@ __global__ void face_reduce_kernel(S* __restrict__ grad, const Geom g,
     }
 }
 
-// Face values of one adjoint pass of depth T (levels 0..T-1 of the pass: level 0
-// is the pass input, level s the input after s transposed sweeps): c * lambda_s
-// at the cells next to each of the six faces, into row sweep0 + s of the face
-// buffer (layout of face_reduce_kernel).  Level s on the face layer depends on
-// level 0 within s cells of it, so a band of T layers along the face normal and
-// T - 1 halo cells along the face holds everything a tile of the face needs.
-// The levels are computed in shared memory with the arithmetic of the sweeps
-// (the six neighbours in Eq. 1's order of the absolute axes, then the product by
-// RN(1/6); a zero boundary), so the values are bit-identical to the levels the
-// pass itself computes.  Grid: (tiles of 32 cells along u, of 8 along v, 6
-// faces); face f has normal axis f / 2 and lies at the low (f even) or high end.
-template <class S>
-__global__ void __launch_bounds__(256) face_band_kernel(const S* __restrict__ src, const Geom g,
-                                                        S* __restrict__ fbuf, long long fstride,
-                                                        int sweep0, int T) {
-    // block (32, 8): thread (tu, tv) walks the band's cells with strides 32 and 8
-    constexpr int TU = 32, TV = 8;
-    extern __shared__ __align__(16) unsigned char band_smem[];
-    const int tu = threadIdx.x, tv = threadIdx.y;
-    const int face = blockIdx.z;
-    const int ax = face / 2;            // normal axis: 0 x, 1 y, 2 z
-    const bool hi = (face & 1) != 0;    // face at the high end of the axis
-    const int nu = ax == 0 ? g.ny : g.nx;   // face extent: u = y (x faces) or x
-    const int nv = ax == 2 ? g.ny : g.nz;   //              v = y (z faces) or z
-    const int nn = ax == 0 ? g.nx : ax == 1 ? g.ny : g.nz;
-    const int u0 = 1 + (int)blockIdx.x * TU, v0 = 1 + (int)blockIdx.y * TV;
-    if (u0 > nu || v0 > nv) return;
-    const int H = T - 1, BU = TU + 2 * H, BV = TV + 2 * H;
-    const int layer = BU * BV, vol = T * layer;
-    S* cur = reinterpret_cast<S*>(band_smem);
-    S* nxt = cur + vol;
-    const S c6 = sizeof(S) == 8 ? S(0x1.5555555555555p-3) : S(0x1.555556p-3f);
-    const long long fxs = (long long)g.ny * g.nz, fys = (long long)g.nx * g.nz;
-    const long long fzs = (long long)g.nx * g.ny;
-    const long long fbase = ax == 0 ? face * fxs
-                            : ax == 1 ? 2 * fxs + (face - 2) * fys
-                                      : 2 * fxs + 2 * fys + (face - 4) * fzs;
-    const int urow = ax == 0 ? g.ny : g.nx;  // face-buffer row length along u
-    // grid offsets of one step along u, along v and inward along the normal
-    const long long su = ax == 0 ? g.px : 1;
-    const long long sv = ax == 2 ? g.px : g.plane;
-    const long long sn_abs = ax == 0 ? 1 : ax == 1 ? g.px : g.plane;
-    const long long sn = hi ? -sn_abs : sn_abs;
-    const int w0 = hi ? nn : 1;  // the face layer along the normal
-    const long long origin = ax == 0 ? g.lin(w0, 0, 0) : ax == 1 ? g.lin(0, w0, 0)
-                                                                : g.lin(0, 0, w0);
-
-    // level 0: band cell (n, iu, iv) is n layers in from the face, u = u0 - H + iu
-    for (int n = 0; n < T; ++n) {
-        const bool nin = n < nn;
-        for (int iv = tv; iv < BV; iv += TV) {
-            const int v = v0 - H + iv;
-            const bool vin = nin && v >= 1 && v <= nv;
-            for (int iu = tu; iu < BU; iu += TU) {
-                const int u = u0 - H + iu;
-                S val = S(0);
-                if (vin && u >= 1 && u <= nu) val = src[origin + n * sn + u * su + v * sv];
-                cur[n * layer + iv * BU + iu] = val;
-            }
-        }
-    }
-    __syncthreads();
-    auto store_faces = [&](const S* lv, int s) {
-        const int u = u0 + tu, v = v0 + tv;
-        if (u > nu || v > nv) return;
-        const S lam = lv[(H + tv) * BU + (H + tu)];  // layer 0
-        S* fb = fbuf + (long long)(sweep0 + s) * fstride + fbase;
-        fb[(long long)(v - 1) * urow + (u - 1)] = sizeof(S) == 8
-            ? S(__dmul_rn((double)c6, (double)lam)) : S(__fmul_rn((float)c6, (float)lam));
-    };
-    store_faces(cur, 0);
-    for (int s = 1; s < T; ++s) {
-        // level s on layers 0..T-1-s, within s cells less of halo
-        for (int n = 0; n < T - s; ++n) {
-            const bool nin = n < nn;
-            for (int iv = s + tv; iv < BV - s; iv += TV) {
-                const int v = v0 - H + iv;
-                const bool vin = nin && v >= 1 && v <= nv;
-                for (int iu = s + tu; iu < BU - s; iu += TU) {
-                    const int u = u0 - H + iu;
-                    const int c = n * layer + iv * BU + iu;
-                    S out = S(0);
-                    if (vin && u >= 1 && u <= nu) {
-                        // neighbours along the normal (n - 1 beyond the face is the boundary)
-                        const S nlo = n > 0 ? cur[c - layer] : S(0), nhi = cur[c + layer];
-                        const S am = hi ? nhi : nlo, ap = hi ? nlo : nhi;  // axis -1, +1
-                        const S um = cur[c - 1], up = cur[c + 1];
-                        const S vm = cur[c - BU], vp = cur[c + BU];
-                        S xm, xp, ym, yp, zm, zp;
-                        if (ax == 0) { xm = am; xp = ap; ym = um; yp = up; zm = vm; zp = vp; }
-                        else if (ax == 1) { xm = um; xp = up; ym = am; yp = ap; zm = vm; zp = vp; }
-                        else { xm = um; xp = up; ym = vm; yp = vp; zm = am; zp = ap; }
-                        if constexpr (sizeof(S) == 8) {
-                            double acc = __dadd_rn(xm, xp);
-                            acc = __dadd_rn(acc, ym); acc = __dadd_rn(acc, yp);
-                            acc = __dadd_rn(acc, zm); acc = __dadd_rn(acc, zp);
-                            out = __dmul_rn(acc, (double)c6);
-                        } else {
-                            float acc = __fadd_rn(xm, xp);
-                            acc = __fadd_rn(acc, ym); acc = __fadd_rn(acc, yp);
-                            acc = __fadd_rn(acc, zm); acc = __fadd_rn(acc, zp);
-                            out = __fmul_rn(acc, (float)c6);
-                        }
-                    }
-                    nxt[c] = out;
-                }
-            }
-        }
-        __syncthreads();
-        store_faces(nxt, s);
-        S* tmp = cur;
-        cur = nxt;
-        nxt = tmp;
-        __syncthreads();
-    }
-}
-
-cudaError_t launch_face_band(int dtype, const void* src, const Geom& g, void* fbuf,
-                             long long fstride, int sweep0, int T, cudaStream_t st) {
-    const int H = T - 1;
-    const size_t es = dtype == 0 ? 8 : 4;
-    const size_t smem = 2 * (size_t)T * (32 + 2 * H) * (8 + 2 * H) * es;
-    const dim3 grid((unsigned)((std::max(g.nx, g.ny) + 31) / 32),
-                    (unsigned)((std::max(g.ny, g.nz) + 7) / 8), 6);
-    if (dtype == 0) {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(face_band_kernel<double>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        face_band_kernel<double><<<grid, dim3(32, 8), smem, st>>>(static_cast<const double*>(src), g,
-                                                          static_cast<double*>(fbuf), fstride,
-                                                          sweep0, T);
-    } else {
-        if (smem > 48 * 1024)
-            cudaFuncSetAttribute(face_band_kernel<float>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        face_band_kernel<float><<<grid, dim3(32, 8), smem, st>>>(static_cast<const float*>(src), g,
-                                                         static_cast<float*>(fbuf), fstride,
-                                                         sweep0, T);
-    }
-    return cudaGetLastError();
-}
-
 cudaError_t launch_face_reduce(int dtype, void* grad, const Geom& g, const void* fbuf,
                                long long fstride, int nsweeps, cudaStream_t st) {
     const int threads = 256;

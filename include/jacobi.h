@@ -27,8 +27,10 @@
  * data and is never written by a sweep.
  *
  * Ownership: the caller owns every grid, every device buffer and the stream.
- * The library owns only what a handle holds (plan, tensor-map descriptors and a
- * small device status word), released by the matching destroy call.
+ * The library owns only what a handle holds (plan, tensor-map descriptors, a
+ * small device status word and, once a call needs them, the adjoint's face
+ * buffer and third grid and the pipelined passes' rings), released by the
+ * matching destroy call.
  *
  * Errors: every call returns JAC_OK (0) or a negative JAC_E* code; nothing is
  * thrown across the ABI.  Calls are asynchronous on the handle's stream: a

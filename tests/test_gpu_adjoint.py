@@ -95,3 +95,43 @@ def test_forward_of_autograd_fn_is_the_sweep():
     for ck in (False, True):
         Y = api.jacobi_fn(X, n, 4, ck)
         assert np.array_equal(to_host(Y.contiguous(), "f64"), oracle.sweeps(x, n))
+
+
+@pytest.mark.parametrize("dtype,tol", [("f64", 1e-13), ("f32", 2e-6)])
+def test_adjoint_every_pass_count(dtype, tol):
+    """Passes rotate through three grids and the last one writes A or B: every
+    pass count from 1 to 7 at depths 1 and 2 (each position of the rotation, and
+    the last pass redirected away from the third grid) against the oracle; a
+    second call on the same handle, which reuses the third grid, gives the same
+    bits."""
+    import torch
+    from paper_0912_4506_gb300 import api
+    nx, ny, nz = 19, 11, 7
+    x = inputs.uniform_grid_f64(nx, ny, nz)
+    W = inputs.normal_grid_f64(nx, ny, nz)
+    px = inputs.row_pitch(nx, dtype)
+    for n in range(1, 8):
+        want = oracle.grad_f64(W, n)
+        scale = np.abs(want).max()
+        for t in (1, 2):
+            got = _grad_gpu(x, W, n, t, dtype)
+            assert np.abs(got - want).max() <= tol * scale, (n, t)
+            outs = []
+            lam0 = api.as_grid(to_dev(inputs.to_dtype(W, dtype, px=px), dtype), nx)
+            for face in (0, -1):
+                lam0[face] = 0
+                lam0[:, face] = 0
+            lam0[:, :, 0] = 0
+            lam0[:, :, nx + 1] = 0
+            j = api.Jacobi(api.alloc_like(lam0))
+            for _ in range(2):
+                j.A.copy_(lam0)
+                gb = api.alloc_like(lam0)
+                gb.zero_()
+                out = j.adjoint(gb, n, t)
+                j.check()
+                torch.cuda.synchronize()
+                outs.append((to_host(out, dtype), to_host(gb, dtype)))
+            j.close()
+            assert np.array_equal(outs[0][0], outs[1][0]), (n, t)
+            assert np.array_equal(outs[0][1], outs[1][1]), (n, t)

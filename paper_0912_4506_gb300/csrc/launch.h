@@ -80,6 +80,8 @@ cudaError_t launch_boundary_copy(int dtype, const void* A, void* B, const Geom& 
                                  cudaStream_t st);
 cudaError_t launch_face_reduce(int dtype, void* grad, const Geom& g, const void* fbuf,
                                long long fstride, int nsweeps, cudaStream_t st);
+// Face values of one adjoint pass of depth T (band.cu): FP64 or FP32, T in 1..8
+// (cudaErrorInvalidValue otherwise).
 cudaError_t launch_face_band(int dtype, const void* src, const Geom& g, void* fbuf,
                              long long fstride, int sweep0, int T, cudaStream_t st);
 cudaError_t launch_range_check(const double* A, const Geom& g, int* flag, cudaStream_t st);

@@ -37,7 +37,7 @@
 // rho before the product; rho's planes arrive by TMA beside the grid's).  MODE_ADJ
 // names the adjoint operation for the planner: the adjoint sweep is the plain
 // sweep on lambda with a zero boundary, so it runs on the MODE_PLAIN kernels, and
-// its boundary-gradient face values come from a separate band kernel (aux.cu).
+// its boundary-gradient face values come from a separate band kernel (band.cu).
 #pragma once
 
 #include <type_traits>

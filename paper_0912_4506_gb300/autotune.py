@@ -19,6 +19,13 @@ from . import api
 DEFAULT_CANDIDATES = ((128, 1), (128, 2), (64, 2), (64, 3), (64, 4), (64, 5), (64, 6))
 
 
+def _built(dtype, cand):
+    """The batched kernel has this (tile width, depth); other candidates are
+    skipped rather than timed."""
+    tile_x, t = cand
+    return (tile_x == 64 and t <= 6) or (tile_x == 128 and t <= 2)
+
+
 def cache_path():
     base = os.environ.get("JACOBI_GB300_CACHE",
                           os.path.join(os.path.expanduser("~"), ".cache", "paper_0912_4506_gb300"))
@@ -34,8 +41,10 @@ def _load(path):
         return {}
 
 
-def _key(dev, dtype, shape):
-    return f"{torch.cuda.get_device_name(dev)}|{dtype}|{shape[0]}x{shape[1]}x{shape[2]}"
+def _key(dev, dtype, shape, cands):
+    """Cache key: device, dtype, shape and the candidate set (a new set retunes)."""
+    cs = ",".join(f"{w}x{t}" for w, t in sorted(cands))
+    return f"{torch.cuda.get_device_name(dev)}|{dtype}|{shape[0]}x{shape[1]}x{shape[2]}|{cs}"
 
 
 def _time_shape(shape, dtype, cand, sweeps, device, reps):
@@ -72,7 +81,7 @@ def tune(shapes, dtype="f32", candidates=DEFAULT_CANDIDATES, sweeps=24, device="
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     out, table = [], {}
     for shape in shapes:
-        key = _key(dev, dtype, shape)
+        key = _key(dev, dtype, shape, [tuple(c) for c in candidates if _built(dtype, c)])
         if key in cache and "tile_x" in cache[key]:
             out.append((cache[key]["tile_x"], cache[key]["t"]))
             table[key] = cache[key]
@@ -81,7 +90,7 @@ def tune(shapes, dtype="f32", candidates=DEFAULT_CANDIDATES, sweeps=24, device="
         cells = nx * ny * nz
         # replicas: enough tiles to cover every SM a few times, bounded memory
         reps = max(1, min(64, (4 * sms * 64 * 32) // max(cells // 8, 1) + 1))
-        cands = [tuple(c) for c in candidates]
+        cands = [tuple(c) for c in candidates if _built(dtype, c)]
         if model_params is not None:
             es = {"f32": 4, "bf16": 2}[dtype]
             cands = model.order_candidates(cands, shape, es, **model_params)

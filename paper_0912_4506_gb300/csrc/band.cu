@@ -113,10 +113,11 @@ __device__ __forceinline__ void face_band_tile(const S* __restrict__ src, const 
                         const S am = hi ? nhi : nlo, ap = hi ? nlo : nhi;  // axis -1, +1
                         const S um = cur[c - 1], up = cur[c + 1];
                         const S vm = cur[c - BU], vp = cur[c + BU];
-                        S xm, xp, ym, yp, zm, zp;
-                        if constexpr (AX == 0) { xm = am; xp = ap; ym = um; yp = up; zm = vm; zp = vp; }
-                        else if constexpr (AX == 1) { xm = um; xp = up; ym = am; yp = ap; zm = vm; zp = vp; }
-                        else { xm = um; xp = up; ym = vm; yp = vp; zm = am; zp = ap; }
+                        // u, v and the normal as the absolute axes x, y, z
+                        const S xm = AX == 0 ? am : um, xp = AX == 0 ? ap : up;
+                        const S ym = AX == 0 ? um : AX == 1 ? am : vm;
+                        const S yp = AX == 0 ? up : AX == 1 ? ap : vp;
+                        const S zm = AX == 2 ? am : vm, zp = AX == 2 ? ap : vp;
                         if constexpr (sizeof(S) == 8) {
                             double acc = __dadd_rn(xm, xp);
                             acc = __dadd_rn(acc, ym);

@@ -22,7 +22,7 @@ int floor_div(int a, int b);
 
 // 3D TMA descriptor over the padded grid (nx+2, ny+2, nz+2) at `base` with a
 // (box_x, box_y, 1) box.  Elements outside the padded grid (the row padding and
-// anything beyond the array) read as zero.  False when the driver rejects it.
+// anything beyond the array) read as zero.  False when the CUDA driver rejects it.
 bool encode_grid_map(CUtensorMap* map, int dtype, const Geom& g, const void* base, int box_x,
                      int box_y);
 
